@@ -1,0 +1,146 @@
+/*
+ * gbsh.h — C ABI of the GB300 loop-hafnian engine for Gaussian boson sampling.
+ *
+ * The engine evaluates the loop hafnian lhaf(A) of a complex symmetric N x N matrix, the
+ * quantity behind every pure-state GBS probability (Eq. lhaf-pure of Sec. II:
+ * p(S) = p(vac) |lhaf(filldiag(B_S, gamma_S))|^2 / (s_1! ... s_m!)), by the signed sum over
+ * the 2^{N/2} subsets of index pairs of the algorithm the paper cites for loop hafnians
+ * (Sec. II, O(N^3 2^{N/2})) and benchmarks in Sec. IV. All arithmetic runs in CUDA kernels
+ * for sm_103a; there is no CPU fallback.
+ *
+ * Conventions shared by every entry point
+ *   - Complex numbers are gbsh_c128 {re, im}: the layout of C double _Complex, numpy
+ *     complex128 and torch.complex128.
+ *   - Matrices are row-major with a leading dimension (elements between rows) >= the
+ *     number of columns. Symmetry is assumed, not checked: both triangles are read and
+ *     should be equal. The diagonal holds the loop weights.
+ *   - N = 0 gives lhaf = 1 (the empty matching). Odd N is allowed: the matrix is padded
+ *     internally with one vertex of loop weight 1 and no edges, which leaves the loop
+ *     hafnian unchanged. The largest supported N is GBSH_MAX_N.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream). Work is ordered on it.
+ *   - Every function returns a status code (GBSH_OK = 0, never an exception). After
+ *     GBSH_ECUDA, gbsh_strerror(code) names the last CUDA error of the calling thread.
+ *   - Results are bit-reproducible for a given N on a given GPU model: the subset sum is
+ *     split into fixed chunks whose compensated partial sums are combined in a fixed order.
+ *   - Functions are re-entrant; calls on different streams may run concurrently. Host
+ *     buffers are owned by the caller and only read/written during the call.
+ */
+#ifndef GBSH_H
+#define GBSH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  double re, im;
+} gbsh_c128;
+
+#define GBSH_MAX_N 60
+
+enum {
+  GBSH_OK = 0,
+  GBSH_EINVAL = 1,    /* bad argument: N out of range, null pointer, bad leading dimension */
+  GBSH_ENOMEM = 2,    /* device memory could not be obtained / admission refused */
+  GBSH_ECUDA = 3,     /* a CUDA call failed; see gbsh_strerror */
+  GBSH_ETIMEOUT = 4,  /* a bounded device or host wait gave up */
+  GBSH_PENDING = 5,   /* asynchronous request not finished yet */
+  GBSH_ENOTFOUND = 6  /* unknown request id */
+};
+
+/* Human-readable text for a status code (for GBSH_ECUDA: the last CUDA error of this
+ * thread). The string is static or thread-local; do not free it. */
+const char* gbsh_strerror(int code);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int gbsh_version(void);
+
+/*
+ * gbsh_lhaf — loop hafnian of one matrix (Sec. II, loop hafnian after Eq. lhaf; the
+ * subset-sum algorithm the paper cites and benchmarks in Sec. IV).
+ *   A        N x N matrix, leading dimension lda >= N; host OR device memory (the call
+ *            detects which with cudaPointerGetAttributes; host memory is copied in).
+ *            May be NULL only when N == 0.
+ *   out      host pointer, receives lhaf(A).
+ *   err_est  host pointer or NULL; receives an estimate of the relative rounding error:
+ *            2^-53 * sum_Z (|Re p_Z| + |Im p_Z|) / |lhaf(A)|, i.e. unit roundoff times the
+ *            cancellation ratio of the signed subset sum.
+ *   stream   cudaStream_t. The call synchronises this stream before returning.
+ * Scratch memory (partial sums) is taken from a per-device cache that the library grows
+ * on demand with cudaMalloc and keeps until exit.
+ * Errors: GBSH_EINVAL (N < 0, N > GBSH_MAX_N, lda < N, A/out NULL), GBSH_ENOMEM,
+ * GBSH_ECUDA.
+ */
+int gbsh_lhaf(const gbsh_c128* A, int N, int lda, gbsh_c128* out, double* err_est,
+              void* stream);
+
+/* Bytes of device workspace gbsh_lhaf_async needs for size N (0 for N outside 1..MAX_N). */
+size_t gbsh_lhaf_workspace_size(int N);
+
+/*
+ * gbsh_lhaf_async — gbsh_lhaf with everything on the device and no synchronisation.
+ *   dA          device matrix, leading dimension lda >= N.
+ *   d_out       device pointer to one gbsh_c128, receives lhaf(A).
+ *   d_abs_sum   device pointer to one double or NULL; receives sum_Z |Re p_Z| + |Im p_Z|.
+ *   workspace   device buffer of at least gbsh_lhaf_workspace_size(N) bytes, 256-byte
+ *               aligned, owned by the caller; must not be used by another call that may
+ *               run at the same time.
+ * N == 0 writes 1 to d_out. Errors: GBSH_EINVAL, GBSH_ECUDA (launch errors only; device
+ * faults surface at the caller's next synchronisation).
+ */
+int gbsh_lhaf_async(const gbsh_c128* dA, int N, int lda, gbsh_c128* d_out, double* d_abs_sum,
+                    void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * gbsh_gbs_prob — pure-state GBS probability, Eq. lhaf-pure (Sec. II):
+ *   p(S) = p_vac * |lhaf(filldiag(B_S, gamma_S))|^2 / prod_i s_i!
+ * where B_S repeats row and column i of B s_i times (modes in ascending order) and
+ * gamma_S repeats gamma_i s_i times (Sec. II after Eq. GBS-pure).
+ *   B        M x M kernel matrix (A = B (+) B* of the pure state), leading dimension ldb,
+ *            host or device memory.
+ *   gamma    M fill-vector entries, host or device memory (same kind as B).
+ *   pattern  host array of M photon numbers s_i >= 0 (pattern[i] belongs to mode i).
+ *   p_vac    vacuum probability of the state (Sec. II).
+ *   prob     host pointer, receives p(S).
+ *   lhaf_out host pointer or NULL, receives the loop hafnian itself.
+ * Errors: GBSH_EINVAL (M < 1, ldb < M, negative s_i, sum s_i > GBSH_MAX_N, NULL pointers),
+ * GBSH_ENOMEM, GBSH_ECUDA. Synchronises `stream`.
+ */
+int gbsh_gbs_prob(const gbsh_c128* B, int M, int ldb, const gbsh_c128* gamma,
+                  const int* pattern, double p_vac, double* prob, gbsh_c128* lhaf_out,
+                  void* stream);
+
+/*
+ * gbsh_subset_terms — diagnostic: the individual subset terms p_Z (before the sign
+ * (-1)^{n-|Z|}) of the subset sum for the listed subsets z of the pairs (j, j+n) of A
+ * padded to even size Ne = N + (N odd), n = Ne/2; bit j of z <=> pair j in Z.
+ *   dA   device N x N matrix (lda >= N); d_z device array of `count` subsets (< 2^n);
+ *   d_out device array of `count` gbsh_c128. Synchronises `stream`.
+ */
+int gbsh_subset_terms(const gbsh_c128* dA, int N, int lda, const uint64_t* d_z, int count,
+                      gbsh_c128* d_out, void* stream);
+
+/*
+ * gbsh_visit_counts — diagnostic: runs the subset enumeration of gbsh_lhaf for size N
+ * (N <= 40) and adds 1 to d_counts[z] for every subset z it evaluates (z = 0 is skipped,
+ * its term is zero). d_counts: device array of 2^n unsigned ints, zeroed by the caller.
+ * A correct enumeration leaves every entry but [0] equal to 1. Synchronises `stream`.
+ */
+int gbsh_visit_counts(int N, unsigned* d_counts, void* stream);
+
+/*
+ * gbsh_set_lhaf_tuning — launch shape of the subset kernel for subsequent calls on this
+ * process: warps per CTA (1..16, 0 = default 8) and a cap on the popcount handled by the
+ * many-warp class (0 = largest that fits in shared memory). Subsets above the cap run in
+ * a second launch with fewer warps and larger work areas. Results do not depend on it.
+ */
+int gbsh_set_lhaf_tuning(int warps_per_cta, int kcap);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBSH_H */

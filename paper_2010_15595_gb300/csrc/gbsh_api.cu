@@ -1,0 +1,310 @@
+// C ABI of the loop-hafnian engine (declarations and contracts in include/gbsh.h).
+// Host code only: argument checks, device scratch, launches of the kernels in
+// lhaf_kernels.cu, and the host<->device copies of the synchronous entry points.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/gbsh.h"
+#include "lhaf_kernels.cuh"
+
+namespace {
+
+thread_local cudaError_t t_last_cuda = cudaSuccess;
+
+int cuda_fail(cudaError_t e) {
+  t_last_cuda = e;
+  return e == cudaErrorMemoryAllocation ? GBSH_ENOMEM : GBSH_ECUDA;
+}
+
+#define GBSH_CUDA(call)                         \
+  do {                                          \
+    cudaError_t _e = (call);                    \
+    if (_e != cudaSuccess) return cuda_fail(_e); \
+  } while (0)
+
+int g_tune_warps = 0;
+int g_tune_kcap = 0;
+std::mutex g_tune_mu;
+
+// Per-device scratch for the synchronous entry points: grown on demand, kept until exit.
+// A call holds the device's lock from its first launch to its final synchronisation, so
+// concurrent synchronous calls on one device serialise on the host.
+struct Scratch {
+  std::mutex mu;
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+Scratch g_scratch[64];
+
+int scratch_get(Scratch& s, size_t need, void** out) {
+  if (s.bytes < need) {
+    if (s.ptr) {
+      cudaError_t e = cudaFree(s.ptr);
+      s.ptr = nullptr;
+      s.bytes = 0;
+      if (e != cudaSuccess) return cuda_fail(e);
+    }
+    size_t want = need < (1u << 20) ? (1u << 20) : need;
+    cudaError_t e = cudaMalloc(&s.ptr, want);
+    if (e != cudaSuccess) {
+      s.ptr = nullptr;
+      return cuda_fail(e);
+    }
+    s.bytes = want;
+  }
+  *out = s.ptr;
+  return GBSH_OK;
+}
+
+bool is_device_pointer(const void* p) {
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // clear the sticky-free error of an unknown pointer
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int plan_for(int N, gbsh::LhafPlan* plan) {
+  gbsh::DeviceInfo dev;
+  GBSH_CUDA(gbsh::device_info(&dev));
+  GBSH_CUDA(gbsh::ensure_constants());
+  int w, k;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    w = g_tune_warps;
+    k = g_tune_kcap;
+  }
+  if (!gbsh::make_plan(N, dev, w, k, plan)) return GBSH_EINVAL;
+  return GBSH_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Runs one loop hafnian whose (already device-resident) matrix is base[idx][idx] with
+// diagonal from `diag` (or base), and copies lhaf and sum|p_Z| to the host.
+int run_sync(const gbsh::LhafPlan& plan, const double2* base, int ld, const double2* diag,
+             const int* idx, void* ws, cudaStream_t st, gbsh_c128* out, double* abs_sum) {
+  GBSH_CUDA(gbsh::launch_lhaf(plan, base, ld, diag, idx, ws, st));
+  double res[3];
+  GBSH_CUDA(cudaMemcpyAsync(res, static_cast<char*>(ws) + plan.off_out, sizeof(res),
+                            cudaMemcpyDeviceToHost, st));
+  GBSH_CUDA(cudaStreamSynchronize(st));
+  out->re = res[0];
+  out->im = res[1];
+  if (abs_sum) *abs_sum = res[2];
+  return GBSH_OK;
+}
+
+double err_from(double abs_sum, gbsh_c128 v) {
+  double mag = std::hypot(v.re, v.im);
+  if (mag == 0.0) return INFINITY;
+  return std::ldexp(1.0, -53) * abs_sum / mag;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gbsh_strerror(int code) {
+  switch (code) {
+    case GBSH_OK: return "ok";
+    case GBSH_EINVAL: return "invalid argument";
+    case GBSH_ENOMEM: return "out of device memory";
+    case GBSH_ECUDA: return cudaGetErrorString(t_last_cuda);
+    case GBSH_ETIMEOUT: return "bounded wait timed out";
+    case GBSH_PENDING: return "request pending";
+    case GBSH_ENOTFOUND: return "unknown request";
+    default: return "unknown status";
+  }
+}
+
+int gbsh_version(void) { return 100; }
+
+int gbsh_set_lhaf_tuning(int warps_per_cta, int kcap) {
+  if (warps_per_cta < 0 || warps_per_cta > gbsh::kMaxWarps || kcap < 0) return GBSH_EINVAL;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_warps = warps_per_cta;
+  g_tune_kcap = kcap;
+  return GBSH_OK;
+}
+
+size_t gbsh_lhaf_workspace_size(int N) {
+  if (N < 1 || N > GBSH_MAX_N) return 0;
+  gbsh::LhafPlan plan;
+  if (plan_for(N, &plan) != GBSH_OK) return 0;
+  return plan.bytes;
+}
+
+int gbsh_lhaf(const gbsh_c128* A, int N, int lda, gbsh_c128* out, double* err_est,
+              void* stream) {
+  if (!out || N < 0 || N > GBSH_MAX_N) return GBSH_EINVAL;
+  if (N == 0) {
+    out->re = 1.0;
+    out->im = 0.0;
+    if (err_est) *err_est = 0.0;
+    return GBSH_OK;
+  }
+  if (!A || lda < N) return GBSH_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  gbsh::LhafPlan plan;
+  int rc = plan_for(N, &plan);
+  if (rc != GBSH_OK) return rc;
+  int dev = 0;
+  GBSH_CUDA(cudaGetDevice(&dev));
+  Scratch& s = g_scratch[dev & 63];
+  std::lock_guard<std::mutex> lk(s.mu);
+  const bool on_dev = is_device_pointer(A);
+  const size_t in_off = align256(plan.bytes);
+  const size_t need = on_dev ? plan.bytes : in_off + sizeof(double2) * (size_t)N * N;
+  void* ws = nullptr;
+  rc = scratch_get(s, need, &ws);
+  if (rc != GBSH_OK) return rc;
+  const double2* base = reinterpret_cast<const double2*>(A);
+  int ld = lda;
+  if (!on_dev) {
+    double2* dA = reinterpret_cast<double2*>(static_cast<char*>(ws) + in_off);
+    GBSH_CUDA(cudaMemcpy2DAsync(dA, sizeof(double2) * N, A, sizeof(double2) * lda,
+                                sizeof(double2) * N, N, cudaMemcpyHostToDevice, st));
+    base = dA;
+    ld = N;
+  }
+  double asum = 0.0;
+  rc = run_sync(plan, base, ld, nullptr, nullptr, ws, st, out, &asum);
+  if (rc != GBSH_OK) return rc;
+  if (err_est) *err_est = err_from(asum, *out);
+  return GBSH_OK;
+}
+
+int gbsh_lhaf_async(const gbsh_c128* dA, int N, int lda, gbsh_c128* d_out, double* d_abs_sum,
+                    void* workspace, size_t workspace_bytes, void* stream) {
+  if (!d_out || N < 0 || N > GBSH_MAX_N) return GBSH_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (N == 0) {
+    static const double one[2] = {1.0, 0.0};
+    GBSH_CUDA(cudaMemcpyAsync(d_out, one, sizeof(one), cudaMemcpyHostToDevice, st));
+    if (d_abs_sum) GBSH_CUDA(cudaMemsetAsync(d_abs_sum, 0, sizeof(double), st));
+    return GBSH_OK;
+  }
+  if (!dA || lda < N || !workspace) return GBSH_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(workspace) & 255u) != 0) return GBSH_EINVAL;
+  gbsh::LhafPlan plan;
+  int rc = plan_for(N, &plan);
+  if (rc != GBSH_OK) return rc;
+  if (workspace_bytes < plan.bytes) return GBSH_EINVAL;
+  GBSH_CUDA(gbsh::launch_lhaf(plan, reinterpret_cast<const double2*>(dA), lda, nullptr,
+                              nullptr, workspace, st));
+  const char* res = static_cast<const char*>(workspace) + plan.off_out;
+  GBSH_CUDA(cudaMemcpyAsync(d_out, res, 2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (d_abs_sum)
+    GBSH_CUDA(cudaMemcpyAsync(d_abs_sum, res + 2 * sizeof(double), sizeof(double),
+                              cudaMemcpyDeviceToDevice, st));
+  return GBSH_OK;
+}
+
+int gbsh_gbs_prob(const gbsh_c128* B, int M, int ldb, const gbsh_c128* gamma,
+                  const int* pattern, double p_vac, double* prob, gbsh_c128* lhaf_out,
+                  void* stream) {
+  if (!B || !gamma || !pattern || !prob || M < 1 || ldb < M) return GBSH_EINVAL;
+  long long N = 0;
+  double fact = 1.0;
+  for (int i = 0; i < M; ++i) {
+    if (pattern[i] < 0) return GBSH_EINVAL;
+    N += pattern[i];
+    for (int f = 2; f <= pattern[i]; ++f) fact *= (double)f;
+  }
+  if (N > GBSH_MAX_N) return GBSH_EINVAL;
+  gbsh_c128 l{1.0, 0.0};
+  if (N > 0) {
+    // index list of B_S: mode i repeated s_i times, ascending (Sec. II)
+    std::vector<int> idx;
+    idx.reserve((size_t)N);
+    for (int i = 0; i < M; ++i)
+      for (int r = 0; r < pattern[i]; ++r) idx.push_back(i);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    gbsh::LhafPlan plan;
+    int rc = plan_for((int)N, &plan);
+    if (rc != GBSH_OK) return rc;
+    int dev = 0;
+    GBSH_CUDA(cudaGetDevice(&dev));
+    Scratch& s = g_scratch[dev & 63];
+    std::lock_guard<std::mutex> lk(s.mu);
+    const bool on_dev = is_device_pointer(B);
+    const size_t idx_off = align256(plan.bytes);
+    const size_t b_off = align256(idx_off + sizeof(int) * (size_t)N);
+    const size_t g_off = align256(b_off + (on_dev ? 0 : sizeof(double2) * (size_t)M * M));
+    const size_t need = align256(g_off + (on_dev ? 0 : sizeof(double2) * (size_t)M));
+    void* ws = nullptr;
+    rc = scratch_get(s, need, &ws);
+    if (rc != GBSH_OK) return rc;
+    char* w = static_cast<char*>(ws);
+    int* d_idx = reinterpret_cast<int*>(w + idx_off);
+    GBSH_CUDA(cudaMemcpyAsync(d_idx, idx.data(), sizeof(int) * idx.size(),
+                              cudaMemcpyHostToDevice, st));
+    const double2* dB = reinterpret_cast<const double2*>(B);
+    const double2* dg = reinterpret_cast<const double2*>(gamma);
+    int ld = ldb;
+    if (!on_dev) {
+      double2* b2 = reinterpret_cast<double2*>(w + b_off);
+      double2* g2 = reinterpret_cast<double2*>(w + g_off);
+      GBSH_CUDA(cudaMemcpy2DAsync(b2, sizeof(double2) * M, B, sizeof(double2) * ldb,
+                                  sizeof(double2) * M, M, cudaMemcpyHostToDevice, st));
+      GBSH_CUDA(cudaMemcpyAsync(g2, gamma, sizeof(double2) * M, cudaMemcpyHostToDevice, st));
+      dB = b2;
+      dg = g2;
+      ld = M;
+    }
+    rc = run_sync(plan, dB, ld, dg, d_idx, ws, st, &l, nullptr);
+    if (rc != GBSH_OK) return rc;
+  }
+  if (lhaf_out) *lhaf_out = l;
+  *prob = p_vac * (l.re * l.re + l.im * l.im) / fact;
+  return GBSH_OK;
+}
+
+int gbsh_subset_terms(const gbsh_c128* dA, int N, int lda, const uint64_t* d_z, int count,
+                      gbsh_c128* d_out, void* stream) {
+  if (N < 1 || N > GBSH_MAX_N || !dA || lda < N || count < 0 || (count > 0 && (!d_z || !d_out)))
+    return GBSH_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  gbsh::LhafPlan plan;
+  int rc = plan_for(N, &plan);
+  if (rc != GBSH_OK) return rc;
+  int dev = 0;
+  GBSH_CUDA(cudaGetDevice(&dev));
+  Scratch& s = g_scratch[dev & 63];
+  std::lock_guard<std::mutex> lk(s.mu);
+  void* ws = nullptr;
+  rc = scratch_get(s, plan.bytes, &ws);
+  if (rc != GBSH_OK) return rc;
+  GBSH_CUDA(gbsh::launch_subset_terms(plan, reinterpret_cast<const double2*>(dA), lda, d_z,
+                                      count, reinterpret_cast<double2*>(d_out), ws, st));
+  GBSH_CUDA(cudaStreamSynchronize(st));
+  return GBSH_OK;
+}
+
+int gbsh_visit_counts(int N, unsigned* d_counts, void* stream) {
+  if (N < 1 || N > 40 || !d_counts) return GBSH_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  gbsh::LhafPlan plan;
+  int rc = plan_for(N, &plan);
+  if (rc != GBSH_OK) return rc;
+  int dev = 0;
+  GBSH_CUDA(cudaGetDevice(&dev));
+  Scratch& s = g_scratch[dev & 63];
+  std::lock_guard<std::mutex> lk(s.mu);
+  void* ws = nullptr;
+  rc = scratch_get(s, plan.bytes, &ws);
+  if (rc != GBSH_OK) return rc;
+  GBSH_CUDA(gbsh::launch_visit_count(plan, d_counts, ws, st));
+  GBSH_CUDA(cudaStreamSynchronize(st));
+  return GBSH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,295 @@
+// Per-subset term of the loop-hafnian subset formula, computed by one warp.
+//
+// The loop hafnian of an N x N complex symmetric matrix A (N = 2n after padding) is
+//     lhaf(A) = sum over subsets Z of the n index pairs (j, j+n) of (-1)^{n-|Z|} p_Z,
+//     p_Z     = [lambda^n] det(I - lambda M_Z)^{-1/2} exp( 1/2 sum_j l_j lambda^j ),
+// with M_Z = X_Z A0_Z (A0 = A without its diagonal, X_Z swapping the two halves of the
+// subset's rows) and loop terms l_j = v_Z^T M_Z^{j-1} X_Z v_Z (v = diag A). This is the
+// O(N^3 2^{N/2}) algorithm the paper cites for loop hafnians (Sec. II after
+// Eq. lhaf-pure) and benchmarks in Sec. IV; the paper evaluates its characteristic
+// polynomial by La Budde's method after a Hessenberg reduction (Sec. IV).
+//
+// GB300 design: FP64 is the scarce unit (about two FP64 FMA lanes per SM per clock), so
+// every step is arranged to keep the 32 lanes of each FP64 warp instruction busy and to
+// avoid FP64 work that the formula does not need:
+//   1. Build the bordered (m+1) x (m+1) matrix K' = [[0, v^T], [X v, M]] in shared memory.
+//      Since det(I - lambda K') = det(I - lambda M) (1 - lambda^2 v^T (I - lambda M)^{-1} X v),
+//      the loop terms follow from the ratio of two characteristic polynomials and need no
+//      Krylov matrix-vector products.
+//   2. Reduce K' to upper Hessenberg form by stabilised elementary similarity
+//      transformations (Gaussian elimination with row pivoting), leaving index 0 fixed,
+//      so that the trailing m x m block stays similar to M. Half the flops of Householder.
+//   3. La Budde's recursion over the trailing principal submatrices, in "push" form (each
+//      finished polynomial is scattered into all later ones at once, lanes spread over
+//      (target, coefficient) pairs), truncated at degree n+1. It yields det(I - lambda M)
+//      and det(I - lambda K').
+//   4. Power-series steps with one lane per coefficient: the ratio gives l_j, Newton's
+//      identities give the power traces tr(M^j), and the exp-polynomial recursion gives
+//      p_Z = [lambda^n] exp(sum_j c_j lambda^j), c_j = tr(M^j)/(2j) + l_j/2.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "lhaf_types.cuh"
+
+namespace gbsh {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// ---------------------------------------------------------------- complex helpers
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+// acc + a*b  (4 FMA)
+__device__ __forceinline__ double2 cfma(double2 acc, double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, fma(-a.y, b.y, acc.x)), fma(a.x, b.y, fma(a.y, b.x, acc.y)));
+}
+// acc - a*b  (4 FMA)
+__device__ __forceinline__ double2 cfms(double2 acc, double2 a, double2 b) {
+  return make_double2(fma(-a.x, b.x, fma(a.y, b.y, acc.x)), fma(-a.x, b.y, fma(-a.y, b.x, acc.y)));
+}
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ double2 crecip(double2 a) {
+  double inv = 1.0 / fma(a.x, a.x, a.y * a.y);
+  return make_double2(a.x * inv, -a.y * inv);
+}
+__device__ __forceinline__ double2 shfl_c(double2 v, int src) {
+  return make_double2(__shfl_sync(FULL, v.x, src), __shfl_sync(FULL, v.y, src));
+}
+__device__ __forceinline__ double2 shfl_up_c(double2 v, unsigned d) {
+  return make_double2(__shfl_up_sync(FULL, v.x, d), __shfl_up_sync(FULL, v.y, d));
+}
+__device__ __forceinline__ double2 shfl_down_c(double2 v, unsigned d) {
+  return make_double2(__shfl_down_sync(FULL, v.x, d), __shfl_down_sync(FULL, v.y, d));
+}
+// Magnitude key for pivoting: the larger of |re|, |im| compared through the high word of
+// the IEEE-754 encoding (sign cleared). Integer-only, so pivot search costs no FP64 issue.
+__device__ __forceinline__ unsigned mag_key(double2 a) {
+  unsigned hx = (unsigned)__double2hiint(a.x) & 0x7fffffffu;
+  unsigned hy = (unsigned)__double2hiint(a.y) & 0x7fffffffu;
+  return hx > hy ? hx : hy;
+}
+
+// 1/k for k = 0..63 (entry 0 unused), filled by the host with correctly rounded values.
+// Defined here because this header is included by exactly one translation unit.
+__constant__ double c_inv_int[64];
+
+// Compensated (two-sum) accumulator for the signed subset sum.
+struct DDAcc {
+  double re_hi, re_lo, im_hi, im_lo, abs_sum;
+  __device__ __forceinline__ void zero() { re_hi = re_lo = im_hi = im_lo = abs_sum = 0.0; }
+  __device__ __forceinline__ static void two_sum(double a, double b, double& s, double& e) {
+    s = a + b;
+    double bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+  }
+  __device__ __forceinline__ void add(double2 x) {
+    double s, e;
+    two_sum(re_hi, x.x, s, e); re_hi = s; re_lo += e;
+    two_sum(im_hi, x.y, s, e); im_hi = s; im_lo += e;
+    abs_sum += fabs(x.x) + fabs(x.y);
+  }
+};
+
+// ------------------------------------------------------------------------------------
+// p_Z for subset z (bit j <=> pair (j, j+n) in Z) with k = popcount(z) >= 1.
+// `area` is this warp's shared work area (warp_area_elems(k, n) double2 at least).
+// All 32 lanes must call it; every lane returns the same value.
+// ------------------------------------------------------------------------------------
+__device__ __noinline__ double2 subset_term(const Problem& P, uint64_t z, int k,
+                                            double2* __restrict__ area, int lane) {
+  const int n = P.n;
+  const int m = 2 * k;
+  const int S = m + 1;
+  const int ldh = S | 1;
+  const int D = n + 1;
+  double2* H = area;                              // S x ldh
+  double2* Pl = area + S * ldh;                   // (S+1) x (D+1) polynomial accumulators
+  int* idx = reinterpret_cast<int*>(Pl + (S + 1) * (D + 1));
+
+  // ---- 1. index list of the subset: idx[a] = a-th pair in Z, idx[k+a] = that pair + n
+  {
+    unsigned bits = (unsigned)z;  // n <= 30
+    bool in = (lane < n) && ((bits >> lane) & 1u);
+    unsigned bal = __ballot_sync(FULL, in);
+    if (in) {
+      int pos = __popc(bal & ((1u << lane) - 1u));
+      idx[pos] = lane;
+      idx[k + pos] = lane + n;
+    }
+  }
+  __syncwarp();
+
+  // ---- 1b. K' = [[0, v^T], [X v, X A0_Z]]; row r>=1 of the M block is row (r-1+k) mod m
+  for (int e = lane; e < S * S; e += 32) {
+    int r = e / S, c = e - r * S;
+    double2 val;
+    if (r == 0) {
+      val = (c == 0) ? make_double2(0.0, 0.0) : __ldg(P.v + idx[c - 1]);
+    } else {
+      int rr = r - 1 + k;
+      rr = rr >= m ? rr - m : rr;
+      int rs = idx[rr];
+      val = (c == 0) ? __ldg(P.v + rs) : __ldg(P.A0 + (size_t)rs * P.Ne + idx[c - 1]);
+    }
+    H[r * ldh + c] = val;
+  }
+  // polynomial accumulators: P_0 = 1, P_t = 0
+  for (int e = lane; e < (S + 1) * (D + 1); e += 32)
+    Pl[e] = make_double2(e == 0 ? 1.0 : 0.0, 0.0);
+  __syncwarp();
+
+  // ---- 2. Hessenberg reduction by stabilised elementary similarities (index 0 fixed
+  //         automatically: column c only mixes rows/columns >= c+1).
+  for (int c = 0; c + 2 < S; ++c) {
+    // pivot: largest magnitude in column c among rows c+1..S-1
+    unsigned best = 0u;
+    int brow = c + 1;
+    for (int r = c + 1 + lane; r < S; r += 32) {
+      unsigned mk = mag_key(H[r * ldh + c]);
+      if (mk > best) { best = mk; brow = r; }
+    }
+    unsigned mx = __reduce_max_sync(FULL, best);
+    if (mx == 0u) continue;  // column already zero below the subdiagonal
+    unsigned cand = __ballot_sync(FULL, best == mx);
+    int p = __shfl_sync(FULL, brow, __ffs(cand) - 1);
+    if (p != c + 1) {
+      for (int j = c + lane; j < S; j += 32) {  // swap rows p and c+1 (columns >= c)
+        double2 a = H[p * ldh + j], b = H[(c + 1) * ldh + j];
+        H[p * ldh + j] = b;
+        H[(c + 1) * ldh + j] = a;
+      }
+      __syncwarp();
+      for (int r = lane; r < S; r += 32) {  // swap columns p and c+1
+        double2 a = H[r * ldh + p], b = H[r * ldh + c + 1];
+        H[r * ldh + p] = b;
+        H[r * ldh + c + 1] = a;
+      }
+      __syncwarp();
+    }
+    const double2 rinv = crecip(H[(c + 1) * ldh + c]);
+    // multipliers l_r = H[r][c] / pivot, kept in H[r][c] (below the subdiagonal)
+    for (int r = c + 2 + lane; r < S; r += 32) H[r * ldh + c] = cmul(H[r * ldh + c], rinv);
+    __syncwarp();
+    // rows r >= c+2:  H[r][j] -= l_r H[c+1][j],  j >= c+1
+    {
+      const int C = S - c - 1;
+      const int R = S - c - 2;
+      for (int e = lane; e < R * C; e += 32) {
+        int rr = e / C, jj = e - rr * C;
+        int r = c + 2 + rr, j = c + 1 + jj;
+        H[r * ldh + j] = cfms(H[r * ldh + j], H[r * ldh + c], H[(c + 1) * ldh + j]);
+      }
+    }
+    __syncwarp();
+    // column c+1 += sum_{i >= c+2} column i * l_i   (right multiplication by L^{-1})
+    for (int r = lane; r < S; r += 32) {
+      double2 acc = H[r * ldh + c + 1];
+      for (int i = c + 2; i < S; ++i) acc = cfma(acc, H[r * ldh + i], H[i * ldh + c]);
+      H[r * ldh + c + 1] = acc;
+    }
+    __syncwarp();
+  }
+
+  // ---- 3a. C(a,b) = H[a][b] * prod_{l=a}^{b-1} H[l+1][l]  for a < b, in place.
+  {
+    double2 beta0 = make_double2(1.0, 0.0), beta1 = make_double2(1.0, 0.0);
+    for (int b = 1; b < S; ++b) {
+      const double2 sub = H[b * ldh + b - 1];
+      if (lane < b) {
+        beta0 = cmul(beta0, sub);
+        H[lane * ldh + b] = cmul(H[lane * ldh + b], beta0);
+      }
+      if (lane + 32 < b) {
+        beta1 = cmul(beta1, sub);
+        H[(lane + 32) * ldh + b] = cmul(H[(lane + 32) * ldh + b], beta1);
+      }
+    }
+  }
+  __syncwarp();
+
+  // ---- 3b. La Budde over trailing blocks. P_t = det(I - lambda H[S-t.., S-t..]):
+  //   P_t = (1 - lambda H[a][a]) P_{t-1} - sum_{b=a+1}^{S-1} C(a,b) lambda^{b-a+1} P_{S-1-b},
+  //   a = S - t. Push form: when P_s is final, add its contribution to every P_t, t > s.
+  for (int s = 0; s < S; ++s) {
+    const double2* Ps = Pl + s * (D + 1);
+    const int degs = s < D ? s : D;  // P_s has degree <= s
+    // diagonal term into P_{s+1}: P_{s+1}[d] += P_s[d] - h P_s[d-1]
+    {
+      const int a = S - 1 - s;  // P_{s+1} starts at row a
+      const double2 h = H[a * ldh + a];
+      double2* Pt = Pl + (s + 1) * (D + 1);
+      const int dmax = (s + 1) < D ? (s + 1) : D;
+      for (int d = lane; d <= dmax; d += 32) {
+        double2 acc = Pt[d];
+        if (d <= degs) acc = cadd(acc, Ps[d]);
+        if (d >= 1) acc = cfms(acc, h, Ps[d - 1]);
+        Pt[d] = acc;
+      }
+    }
+    // off-diagonal terms into P_t, t = s+2..S:  P_t[e + t - s] -= C(S-t, S-1-s) P_s[e]
+    {
+      const int nt = S - s - 1;                 // targets t = s+2 .. S
+      const int emax = (degs < D - 2) ? degs : D - 2;
+      if (nt > 0 && emax >= 0) {
+        const int ne = emax + 1;
+        const int bcol = S - 1 - s;
+        for (int f = lane; f < nt * ne; f += 32) {
+          int ti = f / ne, e = f - ti * ne;
+          int t = s + 2 + ti;
+          int d = e + t - s;
+          if (d <= D) {
+            double2* Pt = Pl + t * (D + 1);
+            Pt[d] = cfms(Pt[d], H[(S - t) * ldh + bcol], Ps[e]);
+          }
+        }
+      }
+    }
+    __syncwarp();
+  }
+
+  // ---- 4. series steps, lane d holds coefficient d (d <= D <= 31)
+  const double2 zero = make_double2(0.0, 0.0);
+  const double2 qM = (lane <= D) ? Pl[(S - 1) * (D + 1) + lane] : zero;
+  const double2 qK = (lane <= D) ? Pl[S * (D + 1) + lane] : zero;
+  // (a) r = qK / qM   (qM_0 = 1)
+  double2 r = qK;
+  for (int s = 0; s < D; ++s) {
+    double2 rs = shfl_c(r, s);
+    double2 qs = shfl_up_c(qM, s);
+    if (lane > s) r = cfms(r, qs, rs);
+  }
+  // loop terms l_j = -r_{j+1}
+  double2 lj = shfl_down_c(r, 1);
+  lj = make_double2(-lj.x, -lj.y);
+  // (b) power traces t_j = tr(M^j):  t_j = -j q_j - sum_{i=1}^{j-1} q_i t_{j-i}
+  double2 tr = cscale(qM, -(double)lane);
+  for (int s = 1; s < n; ++s) {
+    double2 ts = shfl_c(tr, s);
+    double2 qs = shfl_up_c(qM, s);
+    if (lane > s) tr = cfms(tr, qs, ts);
+  }
+  // (c) j c_j = (t_j + j l_j) / 2
+  const double2 icj = make_double2(0.5 * fma((double)lane, lj.x, tr.x),
+                                   0.5 * fma((double)lane, lj.y, tr.y));
+  // (d) exp-polynomial: j p_j = sum_{i=1}^{j} i c_i p_{j-i}, p_0 = 1
+  double2 acc = zero;
+  for (int s = 0; s < n; ++s) {
+    double2 ps;
+    if (s == 0) {
+      ps = make_double2(1.0, 0.0);
+    } else {
+      ps = cscale(shfl_c(acc, s), c_inv_int[s]);
+    }
+    double2 ics = shfl_up_c(icj, s);
+    if (lane > s) acc = cfma(acc, ics, ps);
+  }
+  double2 pn = cscale(shfl_c(acc, n), c_inv_int[n]);
+  __syncwarp();
+  return pn;
+}
+
+}  // namespace gbsh

@@ -1,0 +1,333 @@
+// Loop-hafnian kernels for sm_103a (GB300).
+//
+//   expand_problem_kernel   pattern expansion + filldiag (Sec. II: B_S repeats row/column i
+//                           s_i times, Eq. lhaf-pure puts the fill vector on the diagonal),
+//                           padding to even size, diagonal split off into the loop weights.
+//   lhaf_subsets_kernel     the signed sum over pair subsets (the cited O(N^3 2^{N/2})
+//                           subset formula, Sec. II / Sec. IV), one warp per subset, subsets
+//                           visited in Gray-code order inside fixed chunks that warps claim
+//                           from a counter; one compensated partial per chunk.
+//   lhaf_finalize_kernel    fixed-order compensated reduction of the chunk partials.
+//
+// The result depends only on the chunking (a function of N), not on the launch shape or
+// on which warp took which chunk, so it is bit-reproducible.
+#include <mutex>
+
+#include "lhaf_core.cuh"
+#include "lhaf_kernels.cuh"
+
+namespace gbsh {
+
+// ------------------------------------------------------------------ expansion
+// A0[r][c] = base[idx[r]][idx[c]] (r != c), v[r] = diag ? diag[idx[r]] : base[idx[r]][idx[r]].
+// Rows/columns >= N (odd padding) are zero with loop weight 1.
+__global__ void expand_problem_kernel(const double2* __restrict__ base, int ld,
+                                      const double2* __restrict__ diag,
+                                      const int* __restrict__ idx, int N, int Ne,
+                                      double2* __restrict__ A0, double2* __restrict__ v) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int stride = gridDim.x * blockDim.x;
+  for (int e = tid; e < Ne * Ne; e += stride) {
+    int r = e / Ne, c = e - r * Ne;
+    double2 val = make_double2(0.0, 0.0);
+    if (r != c && r < N && c < N) {
+      int ir = idx ? idx[r] : r, ic = idx ? idx[c] : c;
+      val = base[(size_t)ir * ld + ic];
+    }
+    A0[e] = val;
+  }
+  for (int r = tid; r < Ne; r += stride) {
+    double2 w = make_double2(1.0, 0.0);
+    if (r < N) {
+      int ir = idx ? idx[r] : r;
+      w = diag ? diag[ir] : base[(size_t)ir * ld + ir];
+    }
+    v[r] = w;
+  }
+}
+
+// ------------------------------------------------------------------ subset sum
+// kVisit = true replaces the per-subset term by a visit count (enumeration check).
+template <bool kVisit>
+__global__ void __launch_bounds__(32 * kMaxWarps, 1)
+lhaf_subsets_kernel(Problem P, int k_lo, int k_hi, int area_elems, uint64_t chunk_size,
+                    unsigned nchunks, unsigned* __restrict__ counter,
+                    double* __restrict__ partials, unsigned* __restrict__ visits) {
+  extern __shared__ double2 smem[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  double2* area = smem + (size_t)warp * area_elems;
+  const int n = P.n;
+
+  for (;;) {
+    unsigned ch = 0;
+    if (lane == 0) ch = atomicAdd(counter, 1u);
+    ch = __shfl_sync(FULL, ch, 0);
+    if (ch >= nchunks) break;
+    DDAcc acc;
+    acc.zero();
+    const uint64_t i0 = (uint64_t)ch * chunk_size, i1 = i0 + chunk_size;
+    for (uint64_t i = i0; i < i1; ++i) {
+      const uint64_t z = i ^ (i >> 1);  // Gray code: consecutive subsets differ by one pair
+      const int k = __popcll(z);
+      if (k < k_lo || k > k_hi || k == 0) continue;
+      if (kVisit) {
+        if (lane == 0) atomicAdd(visits + z, 1u);
+        continue;
+      }
+      double2 pz = subset_term(P, z, k, area, lane);
+      if ((n - k) & 1) pz = make_double2(-pz.x, -pz.y);
+      acc.add(pz);
+    }
+    if (!kVisit && lane == 0) {
+      double* o = partials + (size_t)ch * 5;
+      o[0] = acc.re_hi; o[1] = acc.re_lo; o[2] = acc.im_hi; o[3] = acc.im_lo; o[4] = acc.abs_sum;
+    }
+  }
+}
+
+// p_Z for a list of subsets (debug / sampled parity). One warp per listed subset.
+__global__ void __launch_bounds__(32 * kMaxWarps, 1)
+subset_terms_kernel(Problem P, int area_elems, const uint64_t* __restrict__ zs, int count,
+                    double2* __restrict__ out) {
+  extern __shared__ double2 smem[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int wpb = blockDim.x >> 5;
+  double2* area = smem + (size_t)warp * area_elems;
+  for (int q = blockIdx.x * wpb + warp; q < count; q += gridDim.x * wpb) {
+    const uint64_t z = zs[q];
+    const int k = __popcll(z);
+    double2 pz = make_double2(P.n == 0 ? 1.0 : 0.0, 0.0);
+    if (k > 0) pz = subset_term(P, z, k, area, lane);
+    if (lane == 0) out[q] = pz;
+  }
+}
+
+// ------------------------------------------------------------------ finalize
+// Sums partials[cls][ch][5] over cls < nclass and ch < nchunks in a fixed order.
+// out[0..1] = lhaf (re, im), out[2] = sum over subsets of |Re p_Z| + |Im p_Z|.
+__global__ void __launch_bounds__(kFinalizeThreads)
+lhaf_finalize_kernel(const double* __restrict__ partials, unsigned nchunks, int nclass,
+                     double* __restrict__ out) {
+  __shared__ double sh[5][kFinalizeThreads];
+  const int t = threadIdx.x;
+  DDAcc a;
+  a.zero();
+  for (int cls = 0; cls < nclass; ++cls) {
+    const double* p = partials + (size_t)cls * nchunks * 5;
+    for (unsigned ch = t; ch < nchunks; ch += kFinalizeThreads) {
+      const double* q = p + (size_t)ch * 5;
+      double s, e;
+      DDAcc::two_sum(a.re_hi, q[0], s, e); a.re_hi = s; a.re_lo += e + q[1];
+      DDAcc::two_sum(a.im_hi, q[2], s, e); a.im_hi = s; a.im_lo += e + q[3];
+      a.abs_sum += q[4];
+    }
+  }
+  sh[0][t] = a.re_hi; sh[1][t] = a.re_lo; sh[2][t] = a.im_hi; sh[3][t] = a.im_lo; sh[4][t] = a.abs_sum;
+  __syncthreads();
+  for (int w = kFinalizeThreads / 2; w > 0; w >>= 1) {
+    if (t < w) {
+      double s, e;
+      DDAcc::two_sum(sh[0][t], sh[0][t + w], s, e); sh[0][t] = s; sh[1][t] += e + sh[1][t + w];
+      DDAcc::two_sum(sh[2][t], sh[2][t + w], s, e); sh[2][t] = s; sh[3][t] += e + sh[3][t + w];
+      sh[4][t] += sh[4][t + w];
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    out[0] = sh[0][0] + sh[1][0];
+    out[1] = sh[2][0] + sh[3][0];
+    out[2] = sh[4][0];
+  }
+}
+
+// ================================================================== host side
+
+namespace {
+std::mutex g_mu;
+bool g_const_done[64] = {};
+DeviceInfo g_info[64];
+bool g_info_done[64] = {};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+}  // namespace
+
+cudaError_t device_info(DeviceInfo* info) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_info_done[dev]) {
+    DeviceInfo d{};
+    e = cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(lhaf_subsets_kernel<false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, d.smem_optin);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(lhaf_subsets_kernel<true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, d.smem_optin);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(subset_terms_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             d.smem_optin);
+    if (e != cudaSuccess) return e;
+    g_info[dev] = d;
+    g_info_done[dev] = true;
+  }
+  *info = g_info[dev];
+  return cudaSuccess;
+}
+
+cudaError_t ensure_constants() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_const_done[dev]) {
+    double inv[64];
+    inv[0] = 0.0;
+    for (int k = 1; k < 64; ++k) inv[k] = 1.0 / (double)k;
+    e = cudaMemcpyToSymbol(c_inv_int, inv, sizeof(inv));
+    if (e != cudaSuccess) return e;
+    g_const_done[dev] = true;
+  }
+  return cudaSuccess;
+}
+
+bool make_plan(int N, const DeviceInfo& dev, int warps_main, int kcap_override, LhafPlan* p) {
+  if (N < 1 || N > kMaxN) return false;
+  LhafPlan plan{};
+  plan.N = N;
+  plan.Ne = N + (N & 1);
+  plan.n = plan.Ne / 2;
+  const int n = plan.n;
+  const size_t limit = (size_t)dev.smem_optin;
+  auto area_bytes = [&](int k) { return (size_t)warp_area_elems(k, n) * sizeof(double2); };
+  int W = warps_main > 0 ? warps_main : 8;
+  if (W > kMaxWarps) W = kMaxWarps;
+  // largest popcount whose work area fits W warps per CTA
+  int kcap = 0;
+  for (int k = 1; k <= n; ++k)
+    if ((size_t)W * area_bytes(k) <= limit) kcap = k;
+  if (kcap_override > 0 && kcap_override < kcap) kcap = kcap_override;
+  plan.nclass = 0;
+  if (kcap >= 1) {
+    plan.cls[plan.nclass++] = ClassPlan{1, kcap, W, warp_area_elems(kcap, n), 0};
+  }
+  if (kcap < n) {
+    int W1 = (int)(limit / area_bytes(n));
+    if (W1 < 1) return false;
+    if (W1 > W) W1 = W;
+    plan.cls[plan.nclass++] = ClassPlan{kcap + 1, n, W1, warp_area_elems(n, n), 0};
+  }
+  for (int c = 0; c < plan.nclass; ++c) {
+    ClassPlan& cp = plan.cls[c];
+    int per_sm = 0;
+    size_t smem = (size_t)cp.warps * cp.area_elems * sizeof(double2);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lhaf_subsets_kernel<false>,
+                                                      32 * cp.warps, smem) != cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+    cp.blocks = per_sm * dev.sm_count;
+  }
+  const uint64_t total = (uint64_t)1 << n;
+  plan.nchunks = (unsigned)(total < kTargetChunks ? total : kTargetChunks);
+  plan.chunk_size = total / plan.nchunks;
+  size_t off = 0;
+  plan.off_A0 = off; off = align256(off + sizeof(double2) * plan.Ne * plan.Ne);
+  plan.off_v = off; off = align256(off + sizeof(double2) * plan.Ne);
+  plan.off_partials = off; off = align256(off + sizeof(double) * 5 * (size_t)kMaxClasses * plan.nchunks);
+  plan.off_counters = off; off = align256(off + sizeof(unsigned) * kMaxClasses);
+  plan.off_out = off; off = align256(off + sizeof(double) * 4);
+  plan.bytes = off;
+  *p = plan;
+  return true;
+}
+
+static Problem problem_of(const LhafPlan& plan, void* ws) {
+  char* b = static_cast<char*>(ws);
+  Problem P;
+  P.A0 = reinterpret_cast<const double2*>(b + plan.off_A0);
+  P.v = reinterpret_cast<const double2*>(b + plan.off_v);
+  P.Ne = plan.Ne;
+  P.n = plan.n;
+  return P;
+}
+
+static cudaError_t launch_expand(const LhafPlan& plan, const double2* base, int ld,
+                                 const double2* diag, const int* idx, void* ws,
+                                 cudaStream_t stream) {
+  char* b = static_cast<char*>(ws);
+  const int elems = plan.Ne * plan.Ne;
+  const int threads = 256;
+  const int blocks = (elems + threads - 1) / threads;
+  expand_problem_kernel<<<blocks, threads, 0, stream>>>(
+      base, ld, diag, idx, plan.N, plan.Ne, reinterpret_cast<double2*>(b + plan.off_A0),
+      reinterpret_cast<double2*>(b + plan.off_v));
+  return cudaGetLastError();
+}
+
+template <bool kVisit>
+static cudaError_t launch_classes(const LhafPlan& plan, void* ws, unsigned* visits,
+                                  cudaStream_t stream) {
+  char* b = static_cast<char*>(ws);
+  unsigned* counters = reinterpret_cast<unsigned*>(b + plan.off_counters);
+  double* partials = reinterpret_cast<double*>(b + plan.off_partials);
+  cudaError_t e = cudaMemsetAsync(counters, 0, sizeof(unsigned) * kMaxClasses, stream);
+  if (e != cudaSuccess) return e;
+  const Problem P = problem_of(plan, ws);
+  for (int c = 0; c < plan.nclass; ++c) {
+    const ClassPlan& cp = plan.cls[c];
+    size_t smem = (size_t)cp.warps * cp.area_elems * sizeof(double2);
+    lhaf_subsets_kernel<kVisit><<<cp.blocks, 32 * cp.warps, smem, stream>>>(
+        P, cp.k_lo, cp.k_hi, cp.area_elems, plan.chunk_size, plan.nchunks, counters + c,
+        partials + (size_t)c * plan.nchunks * 5, visits);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_lhaf(const LhafPlan& plan, const double2* base, int ld, const double2* diag,
+                        const int* idx, void* ws, cudaStream_t stream) {
+  cudaError_t e = launch_expand(plan, base, ld, diag, idx, ws, stream);
+  if (e != cudaSuccess) return e;
+  e = launch_classes<false>(plan, ws, nullptr, stream);
+  if (e != cudaSuccess) return e;
+  char* b = static_cast<char*>(ws);
+  lhaf_finalize_kernel<<<1, kFinalizeThreads, 0, stream>>>(
+      reinterpret_cast<const double*>(b + plan.off_partials), plan.nchunks, plan.nclass,
+      reinterpret_cast<double*>(b + plan.off_out));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_subset_terms(const LhafPlan& plan, const double2* base, int ld,
+                                const uint64_t* z, int count, double2* out, void* ws,
+                                cudaStream_t stream) {
+  cudaError_t e = launch_expand(plan, base, ld, nullptr, nullptr, ws, stream);
+  if (e != cudaSuccess) return e;
+  if (count <= 0) return cudaSuccess;
+  // every listed subset may be the full set: size the area for k = n
+  const int area = warp_area_elems(plan.n, plan.n);
+  DeviceInfo dev;
+  e = device_info(&dev);
+  if (e != cudaSuccess) return e;
+  int W = (int)((size_t)dev.smem_optin / (area * sizeof(double2)));
+  if (W > 4) W = 4;
+  if (W < 1) return cudaErrorInvalidValue;
+  int blocks = (count + W - 1) / W;
+  if (blocks > 4 * dev.sm_count) blocks = 4 * dev.sm_count;
+  subset_terms_kernel<<<blocks, 32 * W, (size_t)W * area * sizeof(double2), stream>>>(
+      problem_of(plan, ws), area, z, count, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_visit_count(const LhafPlan& plan, unsigned* counts, void* ws,
+                               cudaStream_t stream) {
+  return launch_classes<true>(plan, ws, counts, stream);
+}
+
+}  // namespace gbsh

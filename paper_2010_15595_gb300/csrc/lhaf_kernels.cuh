@@ -1,0 +1,62 @@
+// Host-side launch wrappers for the loop-hafnian kernels (definitions in lhaf_kernels.cu).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "lhaf_types.cuh"
+
+namespace gbsh {
+
+constexpr int kMaxWarps = 16;          // warps per CTA of the subset kernel
+constexpr int kFinalizeThreads = 256;  // threads of the finalize kernel
+constexpr int kMaxClasses = 3;         // popcount classes of one evaluation
+constexpr unsigned kTargetChunks = 1u << 16;
+
+// One launch of the subset kernel: subsets with popcount in [k_lo, k_hi], `warps` warps per
+// CTA, each warp owning `area_elems` double2 of shared memory.
+struct ClassPlan {
+  int k_lo, k_hi, warps, area_elems, blocks;
+};
+
+// Everything needed to evaluate one loop hafnian of padded size Ne.
+struct LhafPlan {
+  int N, Ne, n;
+  int nclass;
+  ClassPlan cls[kMaxClasses];
+  unsigned nchunks;
+  uint64_t chunk_size;
+  // workspace layout (byte offsets)
+  size_t off_A0, off_v, off_partials, off_counters, off_out, bytes;
+};
+
+// Device properties cached per device.
+struct DeviceInfo {
+  int sm_count;
+  int smem_optin;  // max dynamic shared memory per block (bytes)
+};
+
+cudaError_t device_info(DeviceInfo* info);
+// Uploads constant tables on the current device (once per device).
+cudaError_t ensure_constants();
+// Builds the launch plan. warps_main = 0 selects the default. Returns false if N is out of
+// range for the available shared memory.
+bool make_plan(int N, const DeviceInfo& dev, int warps_main, int kcap_override, LhafPlan* plan);
+
+// Launches expansion + subset classes + finalize for one problem. `base`, `diag`, `idx` as
+// in expand_problem_kernel. Writes lhaf (re, im) and sum |p_Z| into ws + off_out.
+cudaError_t launch_lhaf(const LhafPlan& plan, const double2* base, int ld, const double2* diag,
+                        const int* idx, void* ws, cudaStream_t stream);
+
+// Debug: p_Z of `count` subsets (device z list) of an already expanded problem.
+cudaError_t launch_subset_terms(const LhafPlan& plan, const double2* base, int ld,
+                                const uint64_t* z, int count, double2* out, void* ws,
+                                cudaStream_t stream);
+
+// Debug: runs the enumeration of launch_lhaf and counts visits of every subset z into
+// counts[2^n] (which must be zeroed by the caller).
+cudaError_t launch_visit_count(const LhafPlan& plan, unsigned* counts, void* ws,
+                               cudaStream_t stream);
+
+}  // namespace gbsh

@@ -1,0 +1,194 @@
+"""Python binding of the loop-hafnian engine's C ABI (include/gbsh.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA kernels of
+libgbsh.so. Matrices may be numpy arrays (host memory) or torch tensors (host or CUDA);
+PyTorch serves as the device-memory and stream provider. The binding raises if the
+compiled library is missing -- there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libgbsh.so")
+
+GBSH_OK, GBSH_EINVAL, GBSH_ENOMEM, GBSH_ECUDA, GBSH_ETIMEOUT, GBSH_PENDING, GBSH_ENOTFOUND = range(7)
+MAX_N = 60
+
+
+class GbshError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {_strerror(code)} (status {code})")
+
+
+class C128(ctypes.Structure):
+    _fields_ = [("re", ctypes.c_double), ("im", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Loads libgbsh.so (built by paper_2010_15595_gb300.build); raises if it is absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    pc = ctypes.POINTER(C128)
+    pd = ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "gbsh_strerror": ([i], ctypes.c_char_p),
+        "gbsh_version": ([], i),
+        "gbsh_lhaf": ([vp, i, i, pc, pd, vp], i),
+        "gbsh_lhaf_workspace_size": ([i], sz),
+        "gbsh_lhaf_async": ([vp, i, i, vp, vp, vp, sz, vp], i),
+        "gbsh_gbs_prob": ([vp, i, i, vp, ctypes.POINTER(ctypes.c_int), d, pd, pc, vp], i),
+        "gbsh_subset_terms": ([vp, i, i, vp, i, vp, vp], i),
+        "gbsh_visit_counts": ([i, vp, vp], i),
+        "gbsh_set_lhaf_tuning": ([i, i], i),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return ["gbsh_strerror", "gbsh_version", "gbsh_lhaf", "gbsh_lhaf_workspace_size",
+            "gbsh_lhaf_async", "gbsh_gbs_prob", "gbsh_subset_terms", "gbsh_visit_counts",
+            "gbsh_set_lhaf_tuning"]
+
+
+def _strerror(code: int) -> str:
+    try:
+        return load().gbsh_strerror(code).decode()
+    except Exception:  # library not loadable: keep the numeric code
+        return "status"
+
+
+def _check(rc: int, what: str):
+    if rc != GBSH_OK:
+        raise GbshError(rc, what)
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+        return 0
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+def _as_matrix(A):
+    """(pointer, N, ld, keepalive) for a square complex128 numpy array or torch tensor."""
+    try:
+        import torch
+        if isinstance(A, torch.Tensor):
+            if A.dtype != torch.complex128 or A.dim() != 2 or A.shape[0] != A.shape[1]:
+                raise ValueError("square complex128 tensor expected")
+            if A.stride(1) != 1:
+                A = A.contiguous()
+            return A.data_ptr(), A.shape[0], A.stride(0), A
+    except ImportError:
+        pass
+    A = np.ascontiguousarray(A, dtype=np.complex128)
+    if A.ndim != 2 or A.shape[0] != A.shape[1]:
+        raise ValueError("square matrix expected")
+    return A.ctypes.data, A.shape[0], A.shape[0], A
+
+
+def version() -> int:
+    return load().gbsh_version()
+
+
+def set_tuning(warps_per_cta: int = 0, kcap: int = 0):
+    _check(load().gbsh_set_lhaf_tuning(warps_per_cta, kcap), "gbsh_set_lhaf_tuning")
+
+
+def lhaf(A, stream=None, return_error=False):
+    """Loop hafnian of a square complex matrix (numpy array or torch tensor, host or CUDA)."""
+    ptr, N, ld, keep = _as_matrix(A)
+    out = C128()
+    err = ctypes.c_double()
+    rc = load().gbsh_lhaf(ctypes.c_void_p(ptr if N else 0), N, max(ld, N), ctypes.byref(out),
+                          ctypes.byref(err), ctypes.c_void_p(_stream_handle(stream)))
+    _check(rc, "gbsh_lhaf")
+    val = complex(out.re, out.im)
+    return (val, err.value) if return_error else val
+
+
+def workspace_size(N: int) -> int:
+    return int(load().gbsh_lhaf_workspace_size(N))
+
+
+def lhaf_async(dA, d_out, workspace, d_abs_sum=None, stream=None):
+    """Device-only variant: dA (CUDA complex128 N x N), d_out (CUDA complex128, >= 1 entry),
+    workspace (CUDA uint8 tensor of >= workspace_size(N) bytes). No synchronisation."""
+    ptr, N, ld, _ = _as_matrix(dA)
+    rc = load().gbsh_lhaf_async(
+        ctypes.c_void_p(ptr), N, ld, ctypes.c_void_p(d_out.data_ptr()),
+        ctypes.c_void_p(d_abs_sum.data_ptr() if d_abs_sum is not None else 0),
+        ctypes.c_void_p(workspace.data_ptr()), workspace.numel() * workspace.element_size(),
+        ctypes.c_void_p(_stream_handle(stream)))
+    _check(rc, "gbsh_lhaf_async")
+
+
+def gbs_prob(B, gamma, pattern, p_vac=1.0, stream=None, return_lhaf=False):
+    """Eq. lhaf-pure: p_vac |lhaf(filldiag(B_S, gamma_S))|^2 / prod s_i!."""
+    bptr, M, ld, keepB = _as_matrix(B)
+    try:
+        import torch
+        is_t = isinstance(gamma, torch.Tensor)
+    except ImportError:
+        is_t = False
+    if is_t:
+        g = gamma.contiguous()
+        gptr = g.data_ptr()
+    else:
+        g = np.ascontiguousarray(gamma, dtype=np.complex128)
+        gptr = g.ctypes.data
+    pat = np.ascontiguousarray(pattern, dtype=np.int32)
+    if pat.shape != (M,):
+        raise ValueError("pattern must have one entry per mode")
+    prob = ctypes.c_double()
+    lh = C128()
+    rc = load().gbsh_gbs_prob(ctypes.c_void_p(bptr), M, ld, ctypes.c_void_p(gptr),
+                              pat.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), float(p_vac),
+                              ctypes.byref(prob), ctypes.byref(lh),
+                              ctypes.c_void_p(_stream_handle(stream)))
+    _check(rc, "gbsh_gbs_prob")
+    return (prob.value, complex(lh.re, lh.im)) if return_lhaf else prob.value
+
+
+def subset_terms(dA, d_z, stream=None):
+    """p_Z for the subsets in d_z (CUDA uint64/int64 tensor); returns a CUDA complex128 tensor."""
+    import torch
+    ptr, N, ld, _ = _as_matrix(dA)
+    out = torch.empty(d_z.numel(), dtype=torch.complex128, device=d_z.device)
+    rc = load().gbsh_subset_terms(ctypes.c_void_p(ptr), N, ld, ctypes.c_void_p(d_z.data_ptr()),
+                                  d_z.numel(), ctypes.c_void_p(out.data_ptr()),
+                                  ctypes.c_void_p(_stream_handle(stream)))
+    _check(rc, "gbsh_subset_terms")
+    return out
+
+
+def visit_counts(N: int, stream=None):
+    """Visit count of every subset z under the enumeration used by lhaf (CUDA int32 tensor)."""
+    import torch
+    n = (N + (N & 1)) // 2
+    counts = torch.zeros(1 << n, dtype=torch.int32, device="cuda")
+    rc = load().gbsh_visit_counts(N, ctypes.c_void_p(counts.data_ptr()),
+                                  ctypes.c_void_p(_stream_handle(stream)))
+    _check(rc, "gbsh_visit_counts")
+    return counts
