@@ -139,6 +139,18 @@ int gbsh_visit_counts(int N, unsigned* d_counts, void* stream);
  */
 int gbsh_set_lhaf_tuning(int warps_per_cta, int kcap);
 
+/*
+ * gbsh_lhaf_plan — launch plan that gbsh_lhaf / gbsh_lhaf_async use for size N on the
+ * current device, under the current tuning. Any output pointer may be NULL.
+ *   nclass     number of subset-kernel launches (popcount classes, 1..3)
+ *   kernels    CUDA kernels launched per evaluation (expansion + classes + finalize)
+ *   warps      warps per CTA of the first class
+ *   kcap       largest popcount of the first class
+ *   nchunks    number of fixed subset chunks (the reduction order depends only on this)
+ * Errors: GBSH_EINVAL for N outside 1..GBSH_MAX_N, GBSH_ECUDA without a device.
+ */
+int gbsh_lhaf_plan(int N, int* nclass, int* kernels, int* warps, int* kcap, int* nchunks);
+
 #ifdef __cplusplus
 }
 #endif

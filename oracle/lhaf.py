@@ -36,6 +36,8 @@ def _load():
             f = getattr(lib, name)
             f.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, dp]
             f.restype = ctypes.c_int
+        lib.orc_lhaf_subset_stats.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, dp, dp]
+        lib.orc_lhaf_subset_stats.restype = ctypes.c_int
         lib.orc_subset_terms.argtypes = [dp, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_uint64), ctypes.c_int,
                                          ctypes.c_int, dp]
@@ -93,6 +95,18 @@ def lhaf_subset(A, nthreads=None, return_abs_sum=False):
         raise ValueError("bad size")
     val = complex(out[0], out[1])
     return (val, float(asum[0])) if return_abs_sum else val
+
+
+def lhaf_subset_stats(A, nthreads=None):
+    """(lhaf, sum_Z |p_Z|, sum_Z |p_Z|^2) by the subset formula in double."""
+    A = _mat(A)
+    out = np.zeros(2)
+    asum = np.zeros(1)
+    sq = np.zeros(1)
+    if _load().orc_lhaf_subset_stats(_ptr(A), A.shape[0], _threads(nthreads), _ptr(out),
+                                     _ptr(asum), _ptr(sq)):
+        raise ValueError("bad size")
+    return complex(out[0], out[1]), float(asum[0]), float(sq[0])
 
 
 def lhaf_subset_ld(A, nthreads=None, return_abs_sum=False):

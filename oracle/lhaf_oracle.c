@@ -113,20 +113,32 @@ static cplx_t_d *pad_even_d(const cplx *A, int N, int *Np) {
     return P;
 }
 
-/* lhaf by the subset formula in double. out = (re, im); abs_sum = sum_Z |p_Z|. */
-int orc_lhaf_subset(const double *A, int N, int nthreads, double *out, double *abs_sum) {
+/* lhaf by the subset formula in double. out = (re, im); abs_sum = sum_Z |p_Z|;
+ * sq_sum = sum_Z |p_Z|^2 (either may be NULL). */
+int orc_lhaf_subset_stats(const double *A, int N, int nthreads, double *out, double *abs_sum,
+                          double *sq_sum) {
     if (N < 0 || N > 64) return 1;
-    if (N == 0) { out[0] = 1; out[1] = 0; if (abs_sum) *abs_sum = 1; return 0; }
+    if (N == 0) {
+        out[0] = 1; out[1] = 0;
+        if (abs_sum) *abs_sum = 1;
+        if (sq_sum) *sq_sum = 1;
+        return 0;
+    }
     int Ne;
     cplx_t_d *P = pad_even_d((const cplx *)A, N, &Ne);
     cplx_t_d r;
-    double as;
-    lhaf_subset_even_d(P, Ne, nthreads, &r, &as);
+    double as, sq;
+    lhaf_subset_even_d(P, Ne, nthreads, &r, &as, &sq);
     free(P);
     out[0] = creal(r);
     out[1] = cimag(r);
     if (abs_sum) *abs_sum = as;
+    if (sq_sum) *sq_sum = sq;
     return 0;
+}
+
+int orc_lhaf_subset(const double *A, int N, int nthreads, double *out, double *abs_sum) {
+    return orc_lhaf_subset_stats(A, N, nthreads, out, abs_sum, NULL);
 }
 
 /* Same formula in long double (80-bit on x86-64, binary128 on aarch64). */
@@ -140,8 +152,8 @@ int orc_lhaf_subset_ld(const double *A, int N, int nthreads, double *out, double
         for (int c = 0; c < N; c++) P[(size_t)r * Ne + c] = Ac[(size_t)r * N + c];
     if (N & 1) P[(size_t)N * Ne + N] = 1.0L;
     cplx_t_ld r;
-    long double as;
-    lhaf_subset_even_ld(P, Ne, nthreads, &r, &as);
+    long double as, sq;
+    lhaf_subset_even_ld(P, Ne, nthreads, &r, &as, &sq);
     free(P);
     out[0] = (double)creall(r);
     out[1] = (double)cimagl(r);

@@ -110,9 +110,10 @@ static inline void FN(acc_add)(REAL *hi, REAL *lo, REAL x) {
     *lo += e;
 }
 
-/* Sum over z in [z0, z1) of sign * p_Z, with compensated re/im and sum |p_Z|. */
+/* Sum over z in [z0, z1) of sign * p_Z, with compensated re/im, sum |p_Z| and
+ * sum |p_Z|^2 (the last two describe the cancellation of the signed sum). */
 static void FN(subset_range)(const FN(cplx_t) *A, int N, uint64_t z0, uint64_t z1,
-                             REAL out[5]) {
+                             REAL out[6]) {
     const int n = N / 2;
     const int mm = N > 0 ? N : 1;
     FN(cplx_t) *buf = (FN(cplx_t) *)malloc(sizeof(FN(cplx_t)) *
@@ -121,46 +122,52 @@ static void FN(subset_range)(const FN(cplx_t) *A, int N, uint64_t z0, uint64_t z
     FN(cplx_t) *M = buf, *P = M + mm * mm, *Ptmp = P + mm * mm;
     FN(cplx_t) *v = Ptmp + mm * mm, *w = v + mm, *u = w + mm, *utmp = u + mm;
     FN(cplx_t) *c = utmp + mm, *p = c + (n + 1);
-    REAL re_hi = 0, re_lo = 0, im_hi = 0, im_lo = 0, abs_sum = 0;
+    REAL re_hi = 0, re_lo = 0, im_hi = 0, im_lo = 0, abs_sum = 0, sq_sum = 0;
     for (uint64_t z = z0; z < z1; z++) {
         int k = __builtin_popcountll(z);
         FN(cplx_t) pz = FN(subset_pz)(A, N, z, M, P, Ptmp, v, w, u, utmp, c, p, idx);
         REAL sgn = ((n - k) & 1) ? -1 : 1;
         FN(acc_add)(&re_hi, &re_lo, sgn * CAT(creal, RSUF)(pz));
         FN(acc_add)(&im_hi, &im_lo, sgn * CAT(cimag, RSUF)(pz));
-        abs_sum += CAT(cabs, RSUF)(pz);
+        REAL a = CAT(cabs, RSUF)(pz);
+        abs_sum += a;
+        sq_sum += a * a;
     }
     out[0] = re_hi; out[1] = re_lo; out[2] = im_hi; out[3] = im_lo; out[4] = abs_sum;
+    out[5] = sq_sum;
     free(buf);
     free(idx);
 }
 
 /* Full loop hafnian by the subset formula. A is row-major N x N (N already even).
- * out = lhaf, *abs_sum = sum_Z |p_Z| (the cancellation scale of the signed sum).  */
+ * out = lhaf, *abs_sum = sum_Z |p_Z| (the cancellation scale of the signed sum),
+ * *sq_sum = sum_Z |p_Z|^2.  */
 static void FN(lhaf_subset_even)(const FN(cplx_t) *A, int N, int nthreads,
-                                 FN(cplx_t) *out, REAL *abs_sum) {
+                                 FN(cplx_t) *out, REAL *abs_sum, REAL *sq_sum) {
     const int n = N / 2;
     const uint64_t total = (uint64_t)1 << n;
     /* fixed block decomposition: the partial sums do not depend on nthreads */
     const uint64_t nblk = total < 4096 ? total : 4096;
-    REAL *part = (REAL *)calloc((size_t)nblk * 5, sizeof(REAL));
+    REAL *part = (REAL *)calloc((size_t)nblk * 6, sizeof(REAL));
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 1)
     for (long long b = 0; b < (long long)nblk; b++) {
         uint64_t z0 = total * (uint64_t)b / nblk, z1 = total * (uint64_t)(b + 1) / nblk;
-        FN(subset_range)(A, N, z0, z1, part + 5 * b);
+        FN(subset_range)(A, N, z0, z1, part + 6 * b);
     }
-    REAL re_hi = 0, re_lo = 0, im_hi = 0, im_lo = 0, as = 0;
+    REAL re_hi = 0, re_lo = 0, im_hi = 0, im_lo = 0, as = 0, sq = 0;
     for (uint64_t b = 0; b < nblk; b++) {
-        FN(acc_add)(&re_hi, &re_lo, part[5 * b + 0]);
-        re_lo += part[5 * b + 1];
-        FN(acc_add)(&im_hi, &im_lo, part[5 * b + 2]);
-        im_lo += part[5 * b + 3];
-        as += part[5 * b + 4];
+        FN(acc_add)(&re_hi, &re_lo, part[6 * b + 0]);
+        re_lo += part[6 * b + 1];
+        FN(acc_add)(&im_hi, &im_lo, part[6 * b + 2]);
+        im_lo += part[6 * b + 3];
+        as += part[6 * b + 4];
+        sq += part[6 * b + 5];
     }
     free(part);
     *out = (re_hi + re_lo) + (im_hi + im_lo) * (FN(cplx_t))_Complex_I;
     *abs_sum = as;
+    *sq_sum = sq;
 }
 
 #undef FN

@@ -135,6 +135,19 @@ int gbsh_set_lhaf_tuning(int warps_per_cta, int kcap) {
   return GBSH_OK;
 }
 
+int gbsh_lhaf_plan(int N, int* nclass, int* kernels, int* warps, int* kcap, int* nchunks) {
+  if (N < 1 || N > GBSH_MAX_N) return GBSH_EINVAL;
+  gbsh::LhafPlan plan;
+  int rc = plan_for(N, &plan);
+  if (rc != GBSH_OK) return rc;
+  if (nclass) *nclass = plan.nclass;
+  if (kernels) *kernels = plan.nclass + 2;
+  if (warps) *warps = plan.cls[0].warps;
+  if (kcap) *kcap = plan.cls[0].k_hi;
+  if (nchunks) *nchunks = (int)plan.nchunks;
+  return GBSH_OK;
+}
+
 size_t gbsh_lhaf_workspace_size(int N) {
   if (N < 1 || N > GBSH_MAX_N) return 0;
   gbsh::LhafPlan plan;

@@ -54,6 +54,7 @@ def load() -> ctypes.CDLL:
         "gbsh_subset_terms": ([vp, i, i, vp, i, vp, vp], i),
         "gbsh_visit_counts": ([i, vp, vp], i),
         "gbsh_set_lhaf_tuning": ([i, i], i),
+        "gbsh_lhaf_plan": ([i] + [ctypes.POINTER(ctypes.c_int)] * 5, i),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -66,7 +67,7 @@ def load() -> ctypes.CDLL:
 def exported_symbols():
     return ["gbsh_strerror", "gbsh_version", "gbsh_lhaf", "gbsh_lhaf_workspace_size",
             "gbsh_lhaf_async", "gbsh_gbs_prob", "gbsh_subset_terms", "gbsh_visit_counts",
-            "gbsh_set_lhaf_tuning"]
+            "gbsh_set_lhaf_tuning", "gbsh_lhaf_plan"]
 
 
 def _strerror(code: int) -> str:
@@ -126,6 +127,14 @@ def lhaf(A, stream=None, return_error=False):
     _check(rc, "gbsh_lhaf")
     val = complex(out.re, out.im)
     return (val, err.value) if return_error else val
+
+
+def plan(N: int) -> dict:
+    """Launch plan of an N x N evaluation on the current device (see gbsh_lhaf_plan)."""
+    vals = [ctypes.c_int() for _ in range(5)]
+    _check(load().gbsh_lhaf_plan(N, *[ctypes.byref(v) for v in vals]), "gbsh_lhaf_plan")
+    keys = ["nclass", "kernels", "warps", "kcap", "nchunks"]
+    return {k: v.value for k, v in zip(keys, vals)}
 
 
 def workspace_size(N: int) -> int:

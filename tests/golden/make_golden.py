@@ -3,7 +3,8 @@
 Calls only the CPU oracle (oracle/) on inputs from the seeded generators. Each fixture
 stores the input matrix itself (exact decimal round-trip of every double), so a test on
 another host compares against the same bits, plus the oracle's values:
-  lhaf_d   subset formula in double, with abs_sum = sum_Z |p_Z|;
+  lhaf_d   subset formula in double, with abs_sum = sum_Z |p_Z| and
+           sq_sum = sum_Z |p_Z|^2 (the scales of the cancellation in the signed sum);
   lhaf_ld  the same formula in long double (x86-64 80-bit extended), when requested:
            the reference for sizes where the double oracle's own rounding error is near
            the parity tolerance;
@@ -75,9 +76,10 @@ def make(name):
     rec["terms"] = [[int(z), float(p.real), float(p.imag)] for z, p in zip(zs, pz)]
     if do_d:
         t = time.time()
-        v, s = L.lhaf_subset(A, return_abs_sum=True)
+        v, s, sq = L.lhaf_subset_stats(A)
         rec["lhaf_d"] = [v.real, v.imag]
         rec["abs_sum"] = s
+        rec["sq_sum"] = sq
         rec["kappa"] = s / abs(v)
         rec["seconds_d"] = time.time() - t
     if do_ld:
