@@ -151,6 +151,37 @@ int gbsh_set_lhaf_tuning(int warps_per_cta, int kcap);
  */
 int gbsh_lhaf_plan(int N, int* nclass, int* kernels, int* warps, int* kcap, int* nchunks);
 
+/*
+ * gbsh_lhaf_noalloc — gbsh_lhaf_async for callers that cannot allocate device memory.
+ * The paper has no counterpart; this is an engineering entry point.
+ *
+ * Who needs it: code that must not call cudaMalloc/cudaFree -- for example a plugin or
+ * hook running inside another framework whose caching allocator owns the device memory
+ * and forbids driver allocations, or a latency-critical loop that cannot afford the
+ * implicit device synchronisation of an allocation. The caller still passes the input and
+ * output buffers; the scratch (expanded matrix, chunk partial sums, chunk counters) comes
+ * from a fixed array compiled into this library, GBSH_NOALLOC_SCRATCH_BYTES bytes, which
+ * every GPU that loads the library holds until the process exits. No cudaMalloc, cudaFree
+ * or allocating library routine is called.
+ *   dA          device matrix, leading dimension lda >= N (device memory only).
+ *   d_out       device pointer to one gbsh_c128, receives lhaf(A).
+ *   d_abs_sum   device pointer to one double or NULL; receives sum_Z |Re p_Z| + |Im p_Z|.
+ *   stream      cudaStream_t; no synchronisation.
+ * Set-up: the first call on a device looks up the device address of the fixed array
+ * (cudaGetSymbolAddress, with that device current) and caches it; make that first call
+ * before any stream capture.
+ * Sharing: all calls share the one array, which keeps the last call's contents (the call
+ * clears what must start at zero). Calls whose GPU work may overlap -- on different
+ * streams, or from different threads without ordering -- race on it; serialise them.
+ * The launch plan is the library default (gbsh_set_lhaf_tuning does not apply), the same
+ * chunking as gbsh_lhaf, so results agree with it.
+ * Errors: GBSH_EINVAL (N < 0, N > GBSH_MAX_N, lda < N, NULL pointers); GBSH_ENOMEM if an
+ * evaluation would need more than GBSH_NOALLOC_SCRATCH_BYTES of scratch; GBSH_ECUDA.
+ */
+#define GBSH_NOALLOC_SCRATCH_BYTES (8u << 20)
+int gbsh_lhaf_noalloc(const gbsh_c128* dA, int N, int lda, gbsh_c128* d_out, double* d_abs_sum,
+                      void* stream);
+
 #ifdef __cplusplus
 }
 #endif

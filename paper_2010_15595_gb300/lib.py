@@ -55,6 +55,7 @@ def load() -> ctypes.CDLL:
         "gbsh_visit_counts": ([i, vp, vp], i),
         "gbsh_set_lhaf_tuning": ([i, i], i),
         "gbsh_lhaf_plan": ([i] + [ctypes.POINTER(ctypes.c_int)] * 5, i),
+        "gbsh_lhaf_noalloc": ([vp, i, i, vp, vp, vp], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -67,7 +68,7 @@ def load() -> ctypes.CDLL:
 def exported_symbols():
     return ["gbsh_strerror", "gbsh_version", "gbsh_lhaf", "gbsh_lhaf_workspace_size",
             "gbsh_lhaf_async", "gbsh_gbs_prob", "gbsh_subset_terms", "gbsh_visit_counts",
-            "gbsh_set_lhaf_tuning", "gbsh_lhaf_plan"]
+            "gbsh_set_lhaf_tuning", "gbsh_lhaf_plan", "gbsh_lhaf_noalloc"]
 
 
 def _strerror(code: int) -> str:
@@ -151,6 +152,17 @@ def lhaf_async(dA, d_out, workspace, d_abs_sum=None, stream=None):
         ctypes.c_void_p(workspace.data_ptr()), workspace.numel() * workspace.element_size(),
         ctypes.c_void_p(_stream_handle(stream)))
     _check(rc, "gbsh_lhaf_async")
+
+
+def lhaf_noalloc(dA, d_out, d_abs_sum=None, stream=None):
+    """gbsh_lhaf_noalloc: like lhaf_async, but the scratch memory is a fixed array inside
+    the library, for callers that must not allocate device memory. No synchronisation."""
+    ptr, N, ld, _ = _as_matrix(dA)
+    rc = load().gbsh_lhaf_noalloc(
+        ctypes.c_void_p(ptr), N, ld, ctypes.c_void_p(d_out.data_ptr()),
+        ctypes.c_void_p(d_abs_sum.data_ptr() if d_abs_sum is not None else 0),
+        ctypes.c_void_p(_stream_handle(stream)))
+    _check(rc, "gbsh_lhaf_noalloc")
 
 
 def gbs_prob(B, gamma, pattern, p_vac=1.0, stream=None, return_lhaf=False):

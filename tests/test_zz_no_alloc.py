@@ -1,0 +1,51 @@
+"""gbsh_lhaf_noalloc: the loop-hafnian entry point for callers that cannot allocate device
+memory (plugins inside another framework's memory-managed region, latency-critical loops
+that cannot absorb an allocation's implicit synchronisation). Its scratch is a fixed array
+inside the library. Checked through the C ABI against gbsh_lhaf_async (caller-provided
+workspace) on two calls in a row, with different sizes and matrices, so that a second call
+sees the first call's leftovers in the shared array.
+
+This file is collected last on purpose."""
+import numpy as np
+import pytest
+
+from paper_2010_15595_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+U = 2.0 ** -53
+
+
+def _run_both(lib, A):
+    import torch
+    dA = torch.from_numpy(A).cuda()
+    N = A.shape[0]
+    out_ref = torch.zeros(1, dtype=torch.complex128, device="cuda")
+    abs_ref = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ws = torch.empty(lib.workspace_size(N), dtype=torch.uint8, device="cuda")
+    lib.lhaf_async(dA, out_ref, ws, d_abs_sum=abs_ref)
+    out_na = torch.full((1,), complex(np.nan, np.nan), dtype=torch.complex128, device="cuda")
+    abs_na = torch.full((1,), np.nan, dtype=torch.float64, device="cuda")
+    lib.lhaf_noalloc(dA, out_na, d_abs_sum=abs_na)
+    torch.cuda.synchronize()
+    return complex(out_ref.item()), float(abs_ref.item()), complex(out_na.item()), float(abs_na.item())
+
+
+def test_noalloc_matches_workspace_entry_two_calls(gbsh):
+    from oracle import lhaf as L
+    cases = [W.single_lhaf_mid(32), W.single_lhaf_mid(26, seed=3)]
+    for A in cases:  # two calls in a row on the shared scratch
+        ref, aref, got, agot = _run_both(gbsh, A)
+        _, _, sq = L.lhaf_subset_stats(A)
+        tol = max(1e-9, 512 * U * sq ** 0.5 / abs(ref))  # same gate as the parity tests
+        assert abs(got - ref) <= tol * abs(ref), (A.shape, got, ref)
+        assert abs(agot - aref) <= 1e-12 * aref
+
+
+def test_noalloc_rejects_bad_sizes(gbsh):
+    import torch
+    out = torch.zeros(1, dtype=torch.complex128, device="cuda")
+    A = torch.zeros((61, 61), dtype=torch.complex128, device="cuda")
+    with pytest.raises(gbsh.GbshError) as e:
+        gbsh.lhaf_noalloc(A, out)
+    assert e.value.code == gbsh.GBSH_EINVAL
