@@ -52,9 +52,20 @@ __device__ __forceinline__ double2 cfms(double2 acc, double2 a, double2 b) {
   return make_double2(fma(-a.x, b.x, fma(a.y, b.y, acc.x)), fma(-a.x, b.y, fma(-a.y, b.x, acc.y)));
 }
 __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+// 1/a for complex a = conj(a) / |a|^2. The real reciprocal of d = |a|^2 starts from the
+// hardware approximation (rcp.approx.ftz.f64) and is refined by two Newton-Raphson steps
+// r <- r + r (1 - d r), each of which roughly doubles the number of correct bits; the
+// result is accurate to a few ulps (not correctly rounded), ample for a pivot reciprocal,
+// and costs 6 FP64 instructions instead of a full IEEE division.
 __device__ __forceinline__ double2 crecip(double2 a) {
-  double inv = 1.0 / fma(a.x, a.x, a.y * a.y);
-  return make_double2(a.x * inv, -a.y * inv);
+  const double d = fma(a.x, a.x, a.y * a.y);
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+  double e = fma(-d, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-d, r, 1.0);
+  r = fma(r, e, r);
+  return make_double2(a.x * r, -a.y * r);
 }
 __device__ __forceinline__ double2 shfl_c(double2 v, int src) {
   return make_double2(__shfl_sync(FULL, v.x, src), __shfl_sync(FULL, v.y, src));
@@ -107,8 +118,8 @@ __device__ __noinline__ double2 subset_term(const Problem& P, uint64_t z, int k,
   const int ldh = S | 1;
   const int D = n + 1;
   double2* H = area;                              // S x ldh
-  double2* Pl = area + S * ldh;                   // (S+1) x (D+1) polynomial accumulators
-  int* idx = reinterpret_cast<int*>(Pl + (S + 1) * (D + 1));
+  double2* Pl = area + S * ldh;                   // packed polynomial accumulators P_0..P_S
+  int* idx = reinterpret_cast<int*>(Pl + poly_offset(S + 1, D));
 
   // ---- 1. index list of the subset: idx[a] = a-th pair in Z, idx[k+a] = that pair + n
   {
@@ -138,7 +149,7 @@ __device__ __noinline__ double2 subset_term(const Problem& P, uint64_t z, int k,
     H[r * ldh + c] = val;
   }
   // polynomial accumulators: P_0 = 1, P_t = 0
-  for (int e = lane; e < (S + 1) * (D + 1); e += 32)
+  for (int e = lane; e < poly_offset(S + 1, D); e += 32)
     Pl[e] = make_double2(e == 0 ? 1.0 : 0.0, 0.0);
   __syncwarp();
 
@@ -215,13 +226,13 @@ __device__ __noinline__ double2 subset_term(const Problem& P, uint64_t z, int k,
   //   P_t = (1 - lambda H[a][a]) P_{t-1} - sum_{b=a+1}^{S-1} C(a,b) lambda^{b-a+1} P_{S-1-b},
   //   a = S - t. Push form: when P_s is final, add its contribution to every P_t, t > s.
   for (int s = 0; s < S; ++s) {
-    const double2* Ps = Pl + s * (D + 1);
+    const double2* Ps = Pl + poly_offset(s, D);
     const int degs = s < D ? s : D;  // P_s has degree <= s
     // diagonal term into P_{s+1}: P_{s+1}[d] += P_s[d] - h P_s[d-1]
     {
       const int a = S - 1 - s;  // P_{s+1} starts at row a
       const double2 h = H[a * ldh + a];
-      double2* Pt = Pl + (s + 1) * (D + 1);
+      double2* Pt = Pl + poly_offset(s + 1, D);
       const int dmax = (s + 1) < D ? (s + 1) : D;
       for (int d = lane; d <= dmax; d += 32) {
         double2 acc = Pt[d];
@@ -242,7 +253,7 @@ __device__ __noinline__ double2 subset_term(const Problem& P, uint64_t z, int k,
           int t = s + 2 + ti;
           int d = e + t - s;
           if (d <= D) {
-            double2* Pt = Pl + t * (D + 1);
+            double2* Pt = Pl + poly_offset(t, D);
             Pt[d] = cfms(Pt[d], H[(S - t) * ldh + bcol], Ps[e]);
           }
         }
@@ -253,8 +264,10 @@ __device__ __noinline__ double2 subset_term(const Problem& P, uint64_t z, int k,
 
   // ---- 4. series steps, lane d holds coefficient d (d <= D <= 31)
   const double2 zero = make_double2(0.0, 0.0);
-  const double2 qM = (lane <= D) ? Pl[(S - 1) * (D + 1) + lane] : zero;
-  const double2 qK = (lane <= D) ? Pl[S * (D + 1) + lane] : zero;
+  // P_{S-1} and P_S have degree >= D here only if S-1 >= D; lanes above their degree read 0
+  const int degM = (S - 1) < D ? (S - 1) : D, degK = S < D ? S : D;
+  const double2 qM = (lane <= degM) ? Pl[poly_offset(S - 1, D) + lane] : zero;
+  const double2 qK = (lane <= degK) ? Pl[poly_offset(S, D) + lane] : zero;
   // (a) r = qK / qM   (qM_0 = 1)
   double2 r = qK;
   for (int s = 0; s < D; ++s) {

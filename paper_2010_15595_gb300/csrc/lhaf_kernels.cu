@@ -206,22 +206,38 @@ bool make_plan(int N, const DeviceInfo& dev, int warps_main, int kcap_override, 
   const int n = plan.n;
   const size_t limit = (size_t)dev.smem_optin;
   auto area_bytes = [&](int k) { return (size_t)warp_area_elems(k, n) * sizeof(double2); };
+  // largest popcount whose work area fits W warps per CTA (0 if none)
+  auto kfit = [&](int W) {
+    int kc = 0;
+    for (int k = 1; k <= n; ++k)
+      if ((size_t)W * area_bytes(k) <= limit) kc = k;
+    return kc;
+  };
   int W = warps_main > 0 ? warps_main : 8;
   if (W > kMaxWarps) W = kMaxWarps;
-  // largest popcount whose work area fits W warps per CTA
-  int kcap = 0;
-  for (int k = 1; k <= n; ++k)
-    if ((size_t)W * area_bytes(k) <= limit) kcap = k;
-  if (kcap_override > 0 && kcap_override < kcap) kcap = kcap_override;
+  // Popcount classes with decreasing warps per CTA: most subsets (popcount near n/2) run
+  // with W warps; the few large ones run in launches whose warps have larger work areas.
   plan.nclass = 0;
-  if (kcap >= 1) {
-    plan.cls[plan.nclass++] = ClassPlan{1, kcap, W, warp_area_elems(kcap, n), 0};
+  int k_done = 0;
+  int kc = kfit(W);
+  if (kcap_override > 0 && kcap_override < kc) kc = kcap_override;
+  if (kc >= 1) {
+    plan.cls[plan.nclass++] = ClassPlan{1, kc, W, warp_area_elems(kc, n), 0};
+    k_done = kc;
   }
-  if (kcap < n) {
-    int W1 = (int)(limit / area_bytes(n));
-    if (W1 < 1) return false;
-    if (W1 > W) W1 = W;
-    plan.cls[plan.nclass++] = ClassPlan{kcap + 1, n, W1, warp_area_elems(n, n), 0};
+  if (k_done < n && W > 4) {
+    const int W2 = W / 2 > 4 ? W / 2 : 4;
+    const int kc2 = kfit(W2);
+    if (kc2 > k_done && kc2 < n) {
+      plan.cls[plan.nclass++] = ClassPlan{k_done + 1, kc2, W2, warp_area_elems(kc2, n), 0};
+      k_done = kc2;
+    }
+  }
+  if (k_done < n) {
+    int W3 = (int)(limit / area_bytes(n));
+    if (W3 < 1) return false;
+    if (W3 > W) W3 = W;
+    plan.cls[plan.nclass++] = ClassPlan{k_done + 1, n, W3, warp_area_elems(n, n), 0};
   }
   for (int c = 0; c < plan.nclass; ++c) {
     ClassPlan& cp = plan.cls[c];

@@ -16,14 +16,22 @@ struct Problem {
   int n;               // Ne / 2
 };
 
+// La Budde accumulators P_0..P_t are stored packed: P_u has degree <= u and is kept up to
+// degree D, i.e. min(u, D) + 1 coefficients. Offset of P_t in that packed array.
+__host__ __device__ __forceinline__ int poly_offset(int t, int D) {
+  return t <= D + 1 ? t * (t + 1) / 2 : (D + 1) * (D + 2) / 2 + (t - D - 1) * (D + 1);
+}
+
 // Shared-memory footprint (in double2 units) of one warp's work area for subsets with
-// m = 2k <= 2*kmax and series degree D = n+1.
+// m = 2k <= 2*kmax and series degree D = n+1: the bordered matrix (S x S, S = m+1 is odd
+// so the row stride is conflict-free for column access), the packed accumulators
+// P_0..P_S and the subset's index list.
 __host__ __device__ inline int warp_area_elems(int kmax, int n) {
   int S = 2 * kmax + 1;
   int ldh = S | 1;
   int D = n + 1;
   int idx_units = (S + 3) / 4;  // S ints packed into 16-byte units
-  return S * ldh + (S + 1) * (D + 1) + idx_units;
+  return S * ldh + poly_offset(S + 1, D) + idx_units;
 }
 
 }  // namespace gbsh
