@@ -262,6 +262,10 @@ def run_ours(args, rank, world, local_rank):
                             "unit": "TFLOP/s", "frac": ach50 / peak},
                "plan": lib.plan(50)}
 
+    batch = None
+    if args.batch and rank == 0:
+        batch = run_batch_workload(lib, workloads, workmodel, dev, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, count, dt = time_oracle(A, args.cpu_seconds)
@@ -292,10 +296,51 @@ def run_ours(args, rank, world, local_rank):
             "result": {"lhaf": [lhaf_val.real, lhaf_val.imag], "kappa": kappa,
                        "err_est": kappa * 2.0 ** -53},
             "n50": n50,
+            "batch": batch,
             "paper_context": "Fig. 3: N=40 in 44.9 s (23.3k subset-terms/s), N=50 in 2499 s "
                              "(13.4k/s), long double, 96 vCPUs @ 2.345 GHz",
         }
         print(json.dumps(line), flush=True)
+
+
+def run_batch_workload(lib, workloads, workmodel, dev, stream, count=4096):
+    """Batched workload: 4096 loop hafnians of uneven size (N uniform on even 10..30) from
+    one M=100-mode state (r=0.7, Haar U, gamma ~ CN(0, 0.1^2)), up to 3 photons per mode,
+    through gbsh_gbs_prob_batch (device B and gamma). FP64, and complex-FP32 per subset
+    with its error against FP64 reported."""
+    import numpy as np
+    import torch
+    B, gamma = workloads.batch_state()
+    pats = workloads.batch_patterns(count, seed=0)
+    Ns = pats.sum(axis=1)
+    dB = torch.from_numpy(B).to(dev)
+    dg = torch.from_numpy(gamma).to(dev)
+    subsets = int(sum(workmodel.subset_count(int(n)) for n in Ns))
+    flops = float(sum(workmodel.lhaf_flops(int(n)) for n in Ns))
+    res = {"workload": f"{count} loop hafnians, N uniform on even 10..30, M=100 Haar state "
+                       "r=0.7, gamma~CN(0,0.1^2), <=3 photons/mode (gbsh_gbs_prob_batch, "
+                       "host result copy included)", "subset_terms": subsets}
+    out = {}
+    for name, prec in (("fp64", lib.PREC_FP64), ("c32", lib.PREC_C32)):
+        lib.gbs_prob_batch(dB, dg, pats, precision=prec, stream=stream)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        reps = 3
+        for _ in range(reps):
+            probs, lh = lib.gbs_prob_batch(dB, dg, pats, precision=prec, stream=stream)
+        dt = (time.perf_counter() - t) / reps
+        out[name] = lh
+        res[name] = {"seconds": dt, "value": subsets / dt, "unit": UNIT}
+    ach = flops / res["fp64"]["seconds"] / 1e12
+    res["fp64"]["roofline"] = {"bound": "alu", "achieved": ach,
+                               "peak": workmodel.FP64_PEAK_DERIVED_TFLOPS, "unit": "TFLOP/s",
+                               "frac": ach / workmodel.FP64_PEAK_DERIVED_TFLOPS}
+    err = np.abs(out["c32"] - out["fp64"]) / np.abs(out["fp64"])
+    res["c32"]["rel_err_vs_fp64"] = {"median": float(np.median(err)),
+                                     "p99": float(np.quantile(err, 0.99)),
+                                     "max": float(err.max())}
+    res["c32"]["enabled_by_mixed_mode_for_N_le"] = lib.C32_MAX_N
+    return res
 
 
 # ------------------------------------------------------------------ reference arm
@@ -339,6 +384,7 @@ def main(argv=None):
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--n", type=int, default=40)
     p.add_argument("--no-n50", dest="n50", action="store_false")
+    p.add_argument("--no-batch", dest="batch", action="store_false")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--ref-step-seconds", type=float, default=4.0)

@@ -94,6 +94,57 @@ size_t gbsh_lhaf_workspace_size(int N);
 int gbsh_lhaf_async(const gbsh_c128* dA, int N, int lda, gbsh_c128* d_out, double* d_abs_sum,
                     void* workspace, size_t workspace_bytes, void* stream);
 
+/* Per-subset arithmetic of the batched entry points. GBSH_PREC_FP64: complex FP64
+ * throughout. GBSH_PREC_C32: each subset term in complex FP32 (the characteristic
+ * polynomial, traces and exp-polynomial steps), the signed sum over subsets still
+ * compensated in FP64; only for sizes where its measured error is acceptable. */
+#define GBSH_PREC_FP64 0
+#define GBSH_PREC_C32 1
+/* GBSH_PREC_MIXED: complex FP32 per subset only for matrices with N <= GBSH_C32_MAX_N, where
+ * its measured error against the FP64 path stays within 1e-5 relative (measured on the
+ * batched GBS workload: max 5e-7 at N=2, 2.1e-6 at N=4, 2.3e-5 at N=6); FP64 otherwise. */
+#define GBSH_PREC_MIXED 2
+#define GBSH_C32_MAX_N 4
+
+/*
+ * gbsh_lhaf_batch — loop hafnians of `count` matrices of uneven size in one persistent
+ * launch (same algorithm as gbsh_lhaf per matrix).
+ *   A_packed  matrices, each Ns[p] x Ns[p] row-major (leading dimension Ns[p]) starting at
+ *             element offsets[p]; host or device memory (detected; host data is copied in).
+ *   offsets, Ns  host arrays of `count` entries; 0 <= Ns[p] <= GBSH_MAX_N.
+ *   outs      host array of `count` gbsh_c128 (results in input order).
+ *   abs_sums  host array of `count` doubles or NULL: sum_Z |Re p_Z| + |Im p_Z| per matrix.
+ *   precision GBSH_PREC_FP64, GBSH_PREC_C32 (every matrix in FP32 per subset, at the
+ *             caller's risk: use abs_sums to bound the error) or GBSH_PREC_MIXED.
+ * Each matrix's subsets are split into chunks whose size depends only on its own N, so a
+ * matrix's result is bit-identical alone (count = 1) and inside any batch. Problems are
+ * ordered largest first (longest-processing-time order) for the persistent launch.
+ * Synchronises `stream`. Errors: GBSH_EINVAL, GBSH_ENOMEM, GBSH_ECUDA.
+ */
+int gbsh_lhaf_batch(const gbsh_c128* A_packed, const int64_t* offsets, const int* Ns, int count,
+                    gbsh_c128* outs, double* abs_sums, int precision, void* stream);
+
+/*
+ * gbsh_gbs_prob_batch — Eq. lhaf-pure for `count` photon patterns of one kernel matrix B
+ * (Sec. II): p = p_vac[p] |lhaf(filldiag(B_S, gamma_S))|^2 / prod_i s_i!.
+ *   B         M x M (leading dimension ldb), host or device memory.
+ *   gammas    fill vectors, same memory kind as B: problem p uses gammas + p*gamma_stride
+ *             (gamma_stride = 0: one shared vector).
+ *   patterns  host array count x M of photon numbers (row p = pattern of problem p).
+ *   p_vacs    host array of `count` vacuum probabilities, or NULL for 1.
+ *   probs     host array of `count` probabilities; lhafs: host array or NULL.
+ * Synchronises `stream`. Errors: GBSH_EINVAL (bad sizes, negative counts, N > GBSH_MAX_N),
+ * GBSH_ENOMEM, GBSH_ECUDA.
+ */
+int gbsh_gbs_prob_batch(const gbsh_c128* B, int M, int ldb, const gbsh_c128* gammas,
+                        int64_t gamma_stride, const int* patterns, int count,
+                        const double* p_vacs, double* probs, gbsh_c128* lhafs, int precision,
+                        void* stream);
+
+/* Warps per CTA used by the batched kernel for batches whose largest matrix has n_max
+ * pairs (N = 2 n_max), per precision (0 = built-in default). Set by the autotuner. */
+int gbsh_set_batch_tuning(int precision, int n_max, int warps_per_cta);
+
 /*
  * gbsh_gbs_prob — pure-state GBS probability, Eq. lhaf-pure (Sec. II):
  *   p(S) = p_vac * |lhaf(filldiag(B_S, gamma_S))|^2 / prod_i s_i!

@@ -1,10 +1,12 @@
 // C ABI of the loop-hafnian engine (declarations and contracts in include/gbsh.h).
 // Host code only: argument checks, device scratch, launches of the kernels in
 // lhaf_kernels.cu, and the host<->device copies of the synchronous entry points.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <mutex>
+#include <numeric>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -106,6 +108,144 @@ double err_from(double abs_sum, gbsh_c128 v) {
   double mag = std::hypot(v.re, v.im);
   if (mag == 0.0) return INFINITY;
   return std::ldexp(1.0, -53) * abs_sum / mag;
+}
+
+
+// ---------------------------------------------------------------- batched evaluation
+int g_batch_warps[2][gbsh::kMaxN / 2 + 1] = {};  // per precision and n_max; 0 = default
+
+// Workspace layout of a batched evaluation. The first `base_off` bytes belong to the caller
+// (staged inputs: matrices, fill vectors, index lists); the tables, expanded matrices,
+// chunk partials, counter and results follow.
+struct BatchLayout {
+  size_t off_in, off_prob, off_expanded, off_partials, off_counter, off_out, bytes;
+  unsigned total_chunks;
+  int n_max;
+  std::vector<int> order;           // sorted position -> problem index
+  std::vector<gbsh::BatchProblem> table;
+};
+
+BatchLayout batch_layout(const int* Ns, int count, size_t base_off) {
+  BatchLayout L;
+  L.order.resize(count);
+  std::iota(L.order.begin(), L.order.end(), 0);
+  std::stable_sort(L.order.begin(), L.order.end(),
+                   [&](int a, int b) { return Ns[a] > Ns[b]; });
+  L.table.resize(count);
+  unsigned base = 0;
+  size_t exp_elems = 0;
+  L.n_max = 0;
+  for (int q = 0; q < count; ++q) {
+    const int N = Ns[L.order[q]];
+    const int Ne = N + (N & 1);
+    const int n = Ne / 2;
+    gbsh::BatchProblem& P = L.table[q];
+    P.Ne = Ne;
+    P.n = n;
+    P.chunk_size = n > 0 ? gbsh::batch_chunk_size(n) : 1;
+    P.nchunks = n > 0 ? (unsigned)((1ull << n) / P.chunk_size) : 0u;
+    P.chunk_base = base;
+    base += P.nchunks;
+    exp_elems += (size_t)Ne * Ne + Ne;
+    L.n_max = std::max(L.n_max, n);
+  }
+  L.total_chunks = base;
+  size_t off = align256(base_off);
+  L.off_in = off; off = align256(off + sizeof(gbsh::BatchInput) * count);
+  L.off_prob = off; off = align256(off + sizeof(gbsh::BatchProblem) * count);
+  L.off_expanded = off; off = align256(off + sizeof(double2) * exp_elems);
+  L.off_partials = off; off = align256(off + sizeof(double) * 5 * (size_t)L.total_chunks);
+  L.off_counter = off; off = align256(off + sizeof(unsigned));
+  L.off_out = off; off = align256(off + sizeof(double) * 3 * (size_t)count);
+  L.bytes = off;
+  return L;
+}
+
+bool valid_precision(int p) {
+  return p == GBSH_PREC_FP64 || p == GBSH_PREC_C32 || p == GBSH_PREC_MIXED;
+}
+
+// `in` is indexed by problem; the device workspace `ws` already holds whatever the inputs
+// point into. Fills the tables, launches, and copies results back (synchronising).
+int batch_run(BatchLayout& L, const std::vector<gbsh::BatchInput>& in, int count, int precision,
+              void* ws, cudaStream_t st, double* out3) {
+  char* w = static_cast<char*>(ws);
+  std::vector<gbsh::BatchInput> in_sorted(count);
+  double2* exp_base = reinterpret_cast<double2*>(w + L.off_expanded);
+  size_t e_off = 0;
+  for (int q = 0; q < count; ++q) {
+    in_sorted[q] = in[L.order[q]];
+    gbsh::BatchProblem& P = L.table[q];
+    P.A0 = exp_base + e_off;
+    P.v = exp_base + e_off + (size_t)P.Ne * P.Ne;
+    e_off += (size_t)P.Ne * P.Ne + P.Ne;
+  }
+  GBSH_CUDA(cudaMemcpyAsync(w + L.off_in, in_sorted.data(), sizeof(gbsh::BatchInput) * count,
+                            cudaMemcpyHostToDevice, st));
+  GBSH_CUDA(cudaMemcpyAsync(w + L.off_prob, L.table.data(), sizeof(gbsh::BatchProblem) * count,
+                            cudaMemcpyHostToDevice, st));
+  gbsh::DeviceInfo dev;
+  GBSH_CUDA(gbsh::device_info(&dev));
+  GBSH_CUDA(gbsh::ensure_constants());
+  int pref;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    pref = g_batch_warps[precision][L.n_max];
+  }
+  const int W = gbsh::batch_warps_for(std::max(L.n_max, 1), precision, dev, pref);
+  if (W < 1) return GBSH_EINVAL;
+  GBSH_CUDA(gbsh::launch_batch(
+      reinterpret_cast<const gbsh::BatchInput*>(w + L.off_in),
+      reinterpret_cast<const gbsh::BatchProblem*>(w + L.off_prob), count, L.total_chunks,
+      L.n_max, precision, W, reinterpret_cast<unsigned*>(w + L.off_counter),
+      reinterpret_cast<double*>(w + L.off_partials), reinterpret_cast<double*>(w + L.off_out),
+      st));
+  std::vector<double> res(3 * (size_t)count);
+  GBSH_CUDA(cudaMemcpyAsync(res.data(), w + L.off_out, sizeof(double) * res.size(),
+                            cudaMemcpyDeviceToHost, st));
+  GBSH_CUDA(cudaStreamSynchronize(st));
+  for (int q = 0; q < count; ++q)
+    for (int j = 0; j < 3; ++j) out3[3 * (size_t)L.order[q] + j] = res[3 * (size_t)q + j];
+  return GBSH_OK;
+}
+
+
+// Runs the batch in the requested precision. GBSH_PREC_MIXED evaluates the problems with
+// N <= GBSH_C32_MAX_N in complex FP32 and the others in FP64, as two launches that share
+// the workspace (the first `staged` bytes hold the caller's inputs).
+int batch_run_mixed(const int* Ns, const std::vector<gbsh::BatchInput>& in, int count,
+                    int precision, size_t staged, Scratch& s, void** ws, cudaStream_t st,
+                    double* out3) {
+  if (precision != GBSH_PREC_MIXED) {
+    BatchLayout L = batch_layout(Ns, count, staged);
+    int rc = scratch_get(s, L.bytes, ws);
+    if (rc != GBSH_OK) return rc;
+    return batch_run(L, in, count, precision, *ws, st, out3);
+  }
+  for (int pass = 0; pass < 2; ++pass) {
+    const int prec = pass == 0 ? GBSH_PREC_C32 : GBSH_PREC_FP64;
+    std::vector<int> sel;
+    for (int p = 0; p < count; ++p)
+      if ((Ns[p] <= GBSH_C32_MAX_N) == (pass == 0)) sel.push_back(p);
+    if (sel.empty()) continue;
+    std::vector<int> Ns_sel(sel.size());
+    std::vector<gbsh::BatchInput> in_sel(sel.size());
+    for (size_t q = 0; q < sel.size(); ++q) {
+      Ns_sel[q] = Ns[sel[q]];
+      in_sel[q] = in[sel[q]];
+    }
+    BatchLayout L = batch_layout(Ns_sel.data(), (int)sel.size(), staged);
+    void* before = *ws;
+    int rc = scratch_get(s, L.bytes, ws);
+    if (rc != GBSH_OK) return rc;
+    if (*ws != before) return GBSH_ENOMEM;  // staged inputs must not move between passes
+    std::vector<double> o((size_t)3 * sel.size());
+    rc = batch_run(L, in_sel, (int)sel.size(), prec, *ws, st, o.data());
+    if (rc != GBSH_OK) return rc;
+    for (size_t q = 0; q < sel.size(); ++q)
+      for (int j = 0; j < 3; ++j) out3[3 * (size_t)sel[q] + j] = o[3 * q + j];
+  }
+  return GBSH_OK;
 }
 
 }  // namespace
@@ -317,6 +457,131 @@ int gbsh_visit_counts(int N, unsigned* d_counts, void* stream) {
   if (rc != GBSH_OK) return rc;
   GBSH_CUDA(gbsh::launch_visit_count(plan, d_counts, ws, st));
   GBSH_CUDA(cudaStreamSynchronize(st));
+  return GBSH_OK;
+}
+
+int gbsh_lhaf_batch(const gbsh_c128* A_packed, const int64_t* offsets, const int* Ns, int count,
+                    gbsh_c128* outs, double* abs_sums, int precision, void* stream) {
+  if (count < 0 || (count > 0 && (!A_packed || !offsets || !Ns || !outs))) return GBSH_EINVAL;
+  if (!valid_precision(precision)) return GBSH_EINVAL;
+  if (count == 0) return GBSH_OK;
+  int64_t span = 0;
+  for (int p = 0; p < count; ++p) {
+    if (Ns[p] < 0 || Ns[p] > GBSH_MAX_N || offsets[p] < 0) return GBSH_EINVAL;
+    span = std::max<int64_t>(span, offsets[p] + (int64_t)Ns[p] * Ns[p]);
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int dev = 0;
+  GBSH_CUDA(cudaGetDevice(&dev));
+  Scratch& s = g_scratch[dev & 63];
+  std::lock_guard<std::mutex> lk(s.mu);
+  const bool on_dev = is_device_pointer(A_packed);
+  const size_t in_bytes = on_dev ? 0 : sizeof(double2) * (size_t)span;
+  BatchLayout L = batch_layout(Ns, count, in_bytes);
+  void* ws = nullptr;
+  int rc = scratch_get(s, L.bytes, &ws);  // the full layout bounds every sub-batch
+  if (rc != GBSH_OK) return rc;
+  const double2* base = reinterpret_cast<const double2*>(A_packed);
+  if (!on_dev) {
+    GBSH_CUDA(cudaMemcpyAsync(ws, A_packed, in_bytes, cudaMemcpyHostToDevice, st));
+    base = static_cast<const double2*>(ws);
+  }
+  std::vector<gbsh::BatchInput> in(count);
+  for (int p = 0; p < count; ++p) in[p] = gbsh::BatchInput{base + offsets[p], nullptr, nullptr, Ns[p], Ns[p]};
+  std::vector<double> out3(3 * (size_t)count);
+  rc = batch_run_mixed(Ns, in, count, precision, in_bytes, s, &ws, st, out3.data());
+  if (rc != GBSH_OK) return rc;
+  for (int p = 0; p < count; ++p) {
+    outs[p].re = out3[3 * p];
+    outs[p].im = out3[3 * p + 1];
+    if (abs_sums) abs_sums[p] = out3[3 * p + 2];
+  }
+  return GBSH_OK;
+}
+
+int gbsh_gbs_prob_batch(const gbsh_c128* B, int M, int ldb, const gbsh_c128* gammas,
+                        int64_t gamma_stride, const int* patterns, int count,
+                        const double* p_vacs, double* probs, gbsh_c128* lhafs, int precision,
+                        void* stream) {
+  if (count < 0 || (count > 0 && (!B || !gammas || !patterns || !probs))) return GBSH_EINVAL;
+  if (M < 1 || ldb < M || gamma_stride < 0) return GBSH_EINVAL;
+  if (!valid_precision(precision)) return GBSH_EINVAL;
+  if (count == 0) return GBSH_OK;
+  std::vector<int> Ns(count);
+  std::vector<int64_t> idx_off(count + 1, 0);
+  std::vector<double> fact(count, 1.0);
+  for (int p = 0; p < count; ++p) {
+    long long N = 0;
+    for (int i = 0; i < M; ++i) {
+      const int si = patterns[(size_t)p * M + i];
+      if (si < 0) return GBSH_EINVAL;
+      N += si;
+      for (int f = 2; f <= si; ++f) fact[p] *= (double)f;
+    }
+    if (N > GBSH_MAX_N) return GBSH_EINVAL;
+    Ns[p] = (int)N;
+    idx_off[p + 1] = idx_off[p] + N;
+  }
+  std::vector<int> idx((size_t)idx_off[count]);
+  for (int p = 0; p < count; ++p) {
+    int64_t o = idx_off[p];
+    for (int i = 0; i < M; ++i)
+      for (int r = 0; r < patterns[(size_t)p * M + i]; ++r) idx[(size_t)o++] = i;
+  }
+  const int64_t gstride = gamma_stride;
+  const int64_t g_elems = gstride == 0 ? M : gstride * (int64_t)(count - 1) + M;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int dev = 0;
+  GBSH_CUDA(cudaGetDevice(&dev));
+  Scratch& s = g_scratch[dev & 63];
+  std::lock_guard<std::mutex> lk(s.mu);
+  const bool on_dev = is_device_pointer(B);
+  const size_t idx_bytes = align256(sizeof(int) * std::max<size_t>(idx.size(), 1));
+  const size_t b_bytes = on_dev ? 0 : align256(sizeof(double2) * (size_t)M * M);
+  const size_t g_bytes = on_dev ? 0 : align256(sizeof(double2) * (size_t)g_elems);
+  BatchLayout L = batch_layout(Ns.data(), count, idx_bytes + b_bytes + g_bytes);
+  void* ws = nullptr;
+  int rc = scratch_get(s, L.bytes, &ws);
+  if (rc != GBSH_OK) return rc;
+  char* w = static_cast<char*>(ws);
+  int* d_idx = reinterpret_cast<int*>(w);
+  if (!idx.empty())
+    GBSH_CUDA(cudaMemcpyAsync(d_idx, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice, st));
+  const double2* dB = reinterpret_cast<const double2*>(B);
+  const double2* dg = reinterpret_cast<const double2*>(gammas);
+  int ld = ldb;
+  if (!on_dev) {
+    double2* b2 = reinterpret_cast<double2*>(w + idx_bytes);
+    double2* g2 = reinterpret_cast<double2*>(w + idx_bytes + b_bytes);
+    GBSH_CUDA(cudaMemcpy2DAsync(b2, sizeof(double2) * M, B, sizeof(double2) * ldb,
+                                sizeof(double2) * M, M, cudaMemcpyHostToDevice, st));
+    GBSH_CUDA(cudaMemcpyAsync(g2, gammas, sizeof(double2) * (size_t)g_elems,
+                              cudaMemcpyHostToDevice, st));
+    dB = b2;
+    dg = g2;
+    ld = M;
+  }
+  std::vector<gbsh::BatchInput> in(count);
+  for (int p = 0; p < count; ++p)
+    in[p] = gbsh::BatchInput{dB, dg + gstride * p, d_idx + idx_off[p], ld, Ns[p]};
+  std::vector<double> out3(3 * (size_t)count);
+  rc = batch_run_mixed(Ns.data(), in, count, precision, idx_bytes + b_bytes + g_bytes, s, &ws, st,
+                       out3.data());
+  if (rc != GBSH_OK) return rc;
+  for (int p = 0; p < count; ++p) {
+    const double re = out3[3 * p], im = out3[3 * p + 1];
+    if (lhafs) { lhafs[p].re = re; lhafs[p].im = im; }
+    probs[p] = (p_vacs ? p_vacs[p] : 1.0) * (re * re + im * im) / fact[p];
+  }
+  return GBSH_OK;
+}
+
+int gbsh_set_batch_tuning(int precision, int n_max, int warps_per_cta) {
+  if (precision != GBSH_PREC_FP64 && precision != GBSH_PREC_C32) return GBSH_EINVAL;
+  if (n_max < 0 || n_max > gbsh::kMaxN / 2 || warps_per_cta < 0 || warps_per_cta > gbsh::kMaxWarps)
+    return GBSH_EINVAL;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_batch_warps[precision][n_max] = warps_per_cta;
   return GBSH_OK;
 }
 

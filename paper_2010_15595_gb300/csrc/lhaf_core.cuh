@@ -84,6 +84,54 @@ __device__ __forceinline__ unsigned mag_key(double2 a) {
   return hx > hy ? hx : hy;
 }
 
+// ---- complex FP32 versions (per-subset arithmetic of the reduced-precision variant)
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cfma(float2 acc, float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y)));
+}
+__device__ __forceinline__ float2 cfms(float2 acc, float2 a, float2 b) {
+  return make_float2(fmaf(-a.x, b.x, fmaf(a.y, b.y, acc.x)), fmaf(-a.x, b.y, fmaf(-a.y, b.x, acc.y)));
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 crecip(float2 a) {
+  const float inv = 1.0f / fmaf(a.x, a.x, a.y * a.y);
+  return make_float2(a.x * inv, -a.y * inv);
+}
+__device__ __forceinline__ float2 shfl_c(float2 v, int src) {
+  return make_float2(__shfl_sync(FULL, v.x, src), __shfl_sync(FULL, v.y, src));
+}
+__device__ __forceinline__ float2 shfl_up_c(float2 v, unsigned d) {
+  return make_float2(__shfl_up_sync(FULL, v.x, d), __shfl_up_sync(FULL, v.y, d));
+}
+__device__ __forceinline__ float2 shfl_down_c(float2 v, unsigned d) {
+  return make_float2(__shfl_down_sync(FULL, v.x, d), __shfl_down_sync(FULL, v.y, d));
+}
+__device__ __forceinline__ unsigned mag_key(float2 a) {
+  unsigned hx = __float_as_uint(a.x) & 0x7fffffffu;
+  unsigned hy = __float_as_uint(a.y) & 0x7fffffffu;
+  return hx > hy ? hx : hy;
+}
+
+// Scalar-type traits: T is the per-subset complex type (double2 or float2).
+template <class T> struct Cx;
+template <> struct Cx<double2> {
+  using R = double;
+  __device__ __forceinline__ static double2 make(double a, double b) { return make_double2(a, b); }
+  __device__ __forceinline__ static double2 from(double2 v) { return v; }
+  __device__ __forceinline__ static double2 to_d(double2 v) { return v; }
+};
+template <> struct Cx<float2> {
+  using R = float;
+  __device__ __forceinline__ static float2 make(float a, float b) { return make_float2(a, b); }
+  __device__ __forceinline__ static float2 from(double2 v) {
+    return make_float2((float)v.x, (float)v.y);
+  }
+  __device__ __forceinline__ static double2 to_d(float2 v) { return make_double2(v.x, v.y); }
+};
+
 // 1/k for k = 0..63 (entry 0 unused), filled by the host with correctly rounded values.
 // Defined here because this header is included by exactly one translation unit.
 __constant__ double c_inv_int[64];
@@ -107,18 +155,22 @@ struct DDAcc {
 
 // ------------------------------------------------------------------------------------
 // p_Z for subset z (bit j <=> pair (j, j+n) in Z) with k = popcount(z) >= 1.
-// `area` is this warp's shared work area (warp_area_elems(k, n) double2 at least).
+// `area` is this warp's shared work area (warp_area_elems(k, n) elements of T at least).
+// T is the per-subset complex type: double2 (FP64 path) or float2 (reduced-precision
+// variant, whose terms are still accumulated in compensated FP64 by the caller).
 // All 32 lanes must call it; every lane returns the same value.
 // ------------------------------------------------------------------------------------
+template <class T>
 __device__ __noinline__ double2 subset_term(const Problem& P, uint64_t z, int k,
-                                            double2* __restrict__ area, int lane) {
+                                            T* __restrict__ area, int lane) {
+  using R = typename Cx<T>::R;
   const int n = P.n;
   const int m = 2 * k;
   const int S = m + 1;
   const int ldh = S | 1;
   const int D = n + 1;
-  double2* H = area;                              // S x ldh
-  double2* Pl = area + S * ldh;                   // packed polynomial accumulators P_0..P_S
+  T* H = area;                                    // S x ldh
+  T* Pl = area + S * ldh;                         // packed polynomial accumulators P_0..P_S
   int* idx = reinterpret_cast<int*>(Pl + poly_offset(S + 1, D));
 
   // ---- 1. index list of the subset: idx[a] = a-th pair in Z, idx[k+a] = that pair + n
@@ -146,11 +198,11 @@ __device__ __noinline__ double2 subset_term(const Problem& P, uint64_t z, int k,
       int rs = idx[rr];
       val = (c == 0) ? __ldg(P.v + rs) : __ldg(P.A0 + (size_t)rs * P.Ne + idx[c - 1]);
     }
-    H[r * ldh + c] = val;
+    H[r * ldh + c] = Cx<T>::from(val);
   }
   // polynomial accumulators: P_0 = 1, P_t = 0
   for (int e = lane; e < poly_offset(S + 1, D); e += 32)
-    Pl[e] = make_double2(e == 0 ? 1.0 : 0.0, 0.0);
+    Pl[e] = Cx<T>::make(e == 0 ? R(1) : R(0), R(0));
   __syncwarp();
 
   // ---- 2. Hessenberg reduction by stabilised elementary similarities (index 0 fixed
@@ -169,19 +221,19 @@ __device__ __noinline__ double2 subset_term(const Problem& P, uint64_t z, int k,
     int p = __shfl_sync(FULL, brow, __ffs(cand) - 1);
     if (p != c + 1) {
       for (int j = c + lane; j < S; j += 32) {  // swap rows p and c+1 (columns >= c)
-        double2 a = H[p * ldh + j], b = H[(c + 1) * ldh + j];
+        T a = H[p * ldh + j], b = H[(c + 1) * ldh + j];
         H[p * ldh + j] = b;
         H[(c + 1) * ldh + j] = a;
       }
       __syncwarp();
       for (int r = lane; r < S; r += 32) {  // swap columns p and c+1
-        double2 a = H[r * ldh + p], b = H[r * ldh + c + 1];
+        T a = H[r * ldh + p], b = H[r * ldh + c + 1];
         H[r * ldh + p] = b;
         H[r * ldh + c + 1] = a;
       }
       __syncwarp();
     }
-    const double2 rinv = crecip(H[(c + 1) * ldh + c]);
+    const T rinv = crecip(H[(c + 1) * ldh + c]);
     // multipliers l_r = H[r][c] / pivot, kept in H[r][c] (below the subdiagonal)
     for (int r = c + 2 + lane; r < S; r += 32) H[r * ldh + c] = cmul(H[r * ldh + c], rinv);
     __syncwarp();
@@ -198,7 +250,7 @@ __device__ __noinline__ double2 subset_term(const Problem& P, uint64_t z, int k,
     __syncwarp();
     // column c+1 += sum_{i >= c+2} column i * l_i   (right multiplication by L^{-1})
     for (int r = lane; r < S; r += 32) {
-      double2 acc = H[r * ldh + c + 1];
+      T acc = H[r * ldh + c + 1];
       for (int i = c + 2; i < S; ++i) acc = cfma(acc, H[r * ldh + i], H[i * ldh + c]);
       H[r * ldh + c + 1] = acc;
     }
@@ -207,9 +259,9 @@ __device__ __noinline__ double2 subset_term(const Problem& P, uint64_t z, int k,
 
   // ---- 3a. C(a,b) = H[a][b] * prod_{l=a}^{b-1} H[l+1][l]  for a < b, in place.
   {
-    double2 beta0 = make_double2(1.0, 0.0), beta1 = make_double2(1.0, 0.0);
+    T beta0 = Cx<T>::make(R(1), R(0)), beta1 = Cx<T>::make(R(1), R(0));
     for (int b = 1; b < S; ++b) {
-      const double2 sub = H[b * ldh + b - 1];
+      const T sub = H[b * ldh + b - 1];
       if (lane < b) {
         beta0 = cmul(beta0, sub);
         H[lane * ldh + b] = cmul(H[lane * ldh + b], beta0);
@@ -226,16 +278,16 @@ __device__ __noinline__ double2 subset_term(const Problem& P, uint64_t z, int k,
   //   P_t = (1 - lambda H[a][a]) P_{t-1} - sum_{b=a+1}^{S-1} C(a,b) lambda^{b-a+1} P_{S-1-b},
   //   a = S - t. Push form: when P_s is final, add its contribution to every P_t, t > s.
   for (int s = 0; s < S; ++s) {
-    const double2* Ps = Pl + poly_offset(s, D);
+    const T* Ps = Pl + poly_offset(s, D);
     const int degs = s < D ? s : D;  // P_s has degree <= s
     // diagonal term into P_{s+1}: P_{s+1}[d] += P_s[d] - h P_s[d-1]
     {
       const int a = S - 1 - s;  // P_{s+1} starts at row a
-      const double2 h = H[a * ldh + a];
-      double2* Pt = Pl + poly_offset(s + 1, D);
+      const T h = H[a * ldh + a];
+      T* Pt = Pl + poly_offset(s + 1, D);
       const int dmax = (s + 1) < D ? (s + 1) : D;
       for (int d = lane; d <= dmax; d += 32) {
-        double2 acc = Pt[d];
+        T acc = Pt[d];
         if (d <= degs) acc = cadd(acc, Ps[d]);
         if (d >= 1) acc = cfms(acc, h, Ps[d - 1]);
         Pt[d] = acc;
@@ -253,7 +305,7 @@ __device__ __noinline__ double2 subset_term(const Problem& P, uint64_t z, int k,
           int t = s + 2 + ti;
           int d = e + t - s;
           if (d <= D) {
-            double2* Pt = Pl + poly_offset(t, D);
+            T* Pt = Pl + poly_offset(t, D);
             Pt[d] = cfms(Pt[d], H[(S - t) * ldh + bcol], Ps[e]);
           }
         }
@@ -263,46 +315,45 @@ __device__ __noinline__ double2 subset_term(const Problem& P, uint64_t z, int k,
   }
 
   // ---- 4. series steps, lane d holds coefficient d (d <= D <= 31)
-  const double2 zero = make_double2(0.0, 0.0);
+  const T zero = Cx<T>::make(R(0), R(0));
   // P_{S-1} and P_S have degree >= D here only if S-1 >= D; lanes above their degree read 0
   const int degM = (S - 1) < D ? (S - 1) : D, degK = S < D ? S : D;
-  const double2 qM = (lane <= degM) ? Pl[poly_offset(S - 1, D) + lane] : zero;
-  const double2 qK = (lane <= degK) ? Pl[poly_offset(S, D) + lane] : zero;
+  const T qM = (lane <= degM) ? Pl[poly_offset(S - 1, D) + lane] : zero;
+  const T qK = (lane <= degK) ? Pl[poly_offset(S, D) + lane] : zero;
   // (a) r = qK / qM   (qM_0 = 1)
-  double2 r = qK;
+  T r = qK;
   for (int s = 0; s < D; ++s) {
-    double2 rs = shfl_c(r, s);
-    double2 qs = shfl_up_c(qM, s);
+    T rs = shfl_c(r, s);
+    T qs = shfl_up_c(qM, s);
     if (lane > s) r = cfms(r, qs, rs);
   }
   // loop terms l_j = -r_{j+1}
-  double2 lj = shfl_down_c(r, 1);
-  lj = make_double2(-lj.x, -lj.y);
+  T lj = shfl_down_c(r, 1);
+  lj = Cx<T>::make(-lj.x, -lj.y);
   // (b) power traces t_j = tr(M^j):  t_j = -j q_j - sum_{i=1}^{j-1} q_i t_{j-i}
-  double2 tr = cscale(qM, -(double)lane);
+  T tr = cscale(qM, -(R)lane);
   for (int s = 1; s < n; ++s) {
-    double2 ts = shfl_c(tr, s);
-    double2 qs = shfl_up_c(qM, s);
+    T ts = shfl_c(tr, s);
+    T qs = shfl_up_c(qM, s);
     if (lane > s) tr = cfms(tr, qs, ts);
   }
   // (c) j c_j = (t_j + j l_j) / 2
-  const double2 icj = make_double2(0.5 * fma((double)lane, lj.x, tr.x),
-                                   0.5 * fma((double)lane, lj.y, tr.y));
+  const T icj = Cx<T>::make(R(0.5) * fma((R)lane, lj.x, tr.x), R(0.5) * fma((R)lane, lj.y, tr.y));
   // (d) exp-polynomial: j p_j = sum_{i=1}^{j} i c_i p_{j-i}, p_0 = 1
-  double2 acc = zero;
+  T acc = zero;
   for (int s = 0; s < n; ++s) {
-    double2 ps;
+    T ps;
     if (s == 0) {
-      ps = make_double2(1.0, 0.0);
+      ps = Cx<T>::make(R(1), R(0));
     } else {
-      ps = cscale(shfl_c(acc, s), c_inv_int[s]);
+      ps = cscale(shfl_c(acc, s), (R)c_inv_int[s]);
     }
-    double2 ics = shfl_up_c(icj, s);
+    T ics = shfl_up_c(icj, s);
     if (lane > s) acc = cfma(acc, ics, ps);
   }
-  double2 pn = cscale(shfl_c(acc, n), c_inv_int[n]);
+  T pn = cscale(shfl_c(acc, n), (R)c_inv_int[n]);
   __syncwarp();
-  return pn;
+  return Cx<T>::to_d(pn);
 }
 
 }  // namespace gbsh

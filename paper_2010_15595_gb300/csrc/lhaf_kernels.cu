@@ -75,7 +75,7 @@ lhaf_subsets_kernel(Problem P, int k_lo, int k_hi, int area_elems, uint64_t chun
         if (lane == 0) atomicAdd(visits + z, 1u);
         continue;
       }
-      double2 pz = subset_term(P, z, k, area, lane);
+      double2 pz = subset_term<double2>(P, z, k, area, lane);
       if ((n - k) & 1) pz = make_double2(-pz.x, -pz.y);
       acc.add(pz);
     }
@@ -99,7 +99,7 @@ subset_terms_kernel(Problem P, int area_elems, const uint64_t* __restrict__ zs, 
     const uint64_t z = zs[q];
     const int k = __popcll(z);
     double2 pz = make_double2(P.n == 0 ? 1.0 : 0.0, 0.0);
-    if (k > 0) pz = subset_term(P, z, k, area, lane);
+    if (k > 0) pz = subset_term<double2>(P, z, k, area, lane);
     if (lane == 0) out[q] = pz;
   }
 }
@@ -142,6 +142,108 @@ lhaf_finalize_kernel(const double* __restrict__ partials, unsigned nchunks, int 
   }
 }
 
+// ================================================================== batched evaluation
+// Many loop hafnians of uneven size in one persistent launch. Problem p owns global
+// chunks [chunk_base, chunk_base + nchunks); warps claim global chunks from a counter in
+// increasing order, and problems are ordered by decreasing size, so the expensive chunks
+// go first and the tail is made of small ones (longest-processing-time order). Each
+// problem's chunking depends only on its own size, so its result is bit-identical whether
+// it runs alone or inside any batch.
+
+__global__ void expand_batch_kernel(const BatchInput* __restrict__ in,
+                                    const BatchProblem* __restrict__ prob, int count) {
+  const int p = blockIdx.x;
+  if (p >= count) return;
+  const BatchInput I = in[p];
+  const BatchProblem Q = prob[p];
+  double2* A0 = const_cast<double2*>(Q.A0);
+  double2* v = const_cast<double2*>(Q.v);
+  const int N = I.N, Ne = Q.Ne;
+  for (int e = threadIdx.x; e < Ne * Ne; e += blockDim.x) {
+    int r = e / Ne, c = e - r * Ne;
+    double2 val = make_double2(0.0, 0.0);
+    if (r != c && r < N && c < N) {
+      int ir = I.idx ? I.idx[r] : r, ic = I.idx ? I.idx[c] : c;
+      val = I.base[(size_t)ir * I.ld + ic];
+    }
+    A0[e] = val;
+  }
+  for (int r = threadIdx.x; r < Ne; r += blockDim.x) {
+    double2 w = make_double2(1.0, 0.0);
+    if (r < N) {
+      int ir = I.idx ? I.idx[r] : r;
+      w = I.diag ? I.diag[ir] : I.base[(size_t)ir * I.ld + ir];
+    }
+    v[r] = w;
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(32 * kMaxWarps, 1)
+lhaf_batch_kernel(const BatchProblem* __restrict__ prob, int count, unsigned total_chunks,
+                  int area_elems, unsigned* __restrict__ counter,
+                  double* __restrict__ partials) {
+  extern __shared__ double2 smem_raw[];
+  T* smem = reinterpret_cast<T*>(smem_raw);
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  T* area = smem + (size_t)warp * area_elems;
+  for (;;) {
+    unsigned g = 0;
+    if (lane == 0) g = atomicAdd(counter, 1u);
+    g = __shfl_sync(FULL, g, 0);
+    if (g >= total_chunks) break;
+    // problem owning chunk g: last p with chunk_base <= g (bases are increasing)
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (prob[mid].chunk_base <= g) lo = mid; else hi = mid - 1;
+    }
+    const BatchProblem Q = prob[lo];
+    Problem P;
+    P.A0 = Q.A0;
+    P.v = Q.v;
+    P.Ne = Q.Ne;
+    P.n = Q.n;
+    DDAcc acc;
+    acc.zero();
+    const uint64_t i0 = (uint64_t)(g - Q.chunk_base) * Q.chunk_size, i1 = i0 + Q.chunk_size;
+    for (uint64_t i = i0; i < i1; ++i) {
+      const uint64_t z = i ^ (i >> 1);
+      const int k = __popcll(z);
+      if (k == 0) continue;
+      double2 pz = subset_term<T>(P, z, k, area, lane);
+      if ((P.n - k) & 1) pz = make_double2(-pz.x, -pz.y);
+      acc.add(pz);
+    }
+    if (lane == 0) {
+      double* o = partials + (size_t)g * 5;
+      o[0] = acc.re_hi; o[1] = acc.re_lo; o[2] = acc.im_hi; o[3] = acc.im_lo; o[4] = acc.abs_sum;
+    }
+  }
+}
+
+// One thread per problem: its chunk partials in increasing order. out[p] = (re, im, sum|p|).
+__global__ void lhaf_batch_finalize_kernel(const BatchProblem* __restrict__ prob, int count,
+                                           const double* __restrict__ partials,
+                                           double* __restrict__ out) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= count) return;
+  const BatchProblem Q = prob[p];
+  DDAcc a;
+  a.zero();
+  for (unsigned c = 0; c < Q.nchunks; ++c) {
+    const double* q = partials + (size_t)(Q.chunk_base + c) * 5;
+    double s, e;
+    DDAcc::two_sum(a.re_hi, q[0], s, e); a.re_hi = s; a.re_lo += e + q[1];
+    DDAcc::two_sum(a.im_hi, q[2], s, e); a.im_hi = s; a.im_lo += e + q[3];
+    a.abs_sum += q[4];
+  }
+  out[3 * p + 0] = Q.n == 0 ? 1.0 : a.re_hi + a.re_lo;
+  out[3 * p + 1] = Q.n == 0 ? 0.0 : a.im_hi + a.im_lo;
+  out[3 * p + 2] = Q.n == 0 ? 1.0 : a.abs_sum;
+}
+
 // ================================================================== host side
 
 namespace {
@@ -173,6 +275,12 @@ cudaError_t device_info(DeviceInfo* info) {
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(subset_terms_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              d.smem_optin);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(lhaf_batch_kernel<double2>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, d.smem_optin);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(lhaf_batch_kernel<float2>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, d.smem_optin);
     if (e != cudaSuccess) return e;
     g_info[dev] = d;
     g_info_done[dev] = true;
@@ -344,6 +452,65 @@ cudaError_t launch_subset_terms(const LhafPlan& plan, const double2* base, int l
 cudaError_t launch_visit_count(const LhafPlan& plan, unsigned* counts, void* ws,
                                cudaStream_t stream) {
   return launch_classes<true>(plan, ws, counts, stream);
+}
+
+}  // namespace gbsh
+
+namespace gbsh {
+
+int batch_warps_for(int n_max, int precision, const DeviceInfo& dev, int warps_pref) {
+  const int esz = precision == kPrecC32 ? (int)sizeof(float2) : (int)sizeof(double2);
+  const size_t area = (size_t)warp_area_elems(n_max, n_max, esz) * esz;
+  int W = warps_pref > 0 ? warps_pref : 8;
+  if (W > kMaxWarps) W = kMaxWarps;
+  while (W > 1 && (size_t)W * area > (size_t)dev.smem_optin) --W;
+  if ((size_t)W * area > (size_t)dev.smem_optin) return 0;
+  return W;
+}
+
+cudaError_t launch_batch(const BatchInput* d_in, const BatchProblem* d_prob, int count,
+                         unsigned total_chunks, int n_max, int precision, int warps,
+                         unsigned* d_counter, double* d_partials, double* d_out,
+                         cudaStream_t stream) {
+  if (count <= 0) return cudaSuccess;
+  DeviceInfo dev;
+  cudaError_t e = device_info(&dev);
+  if (e != cudaSuccess) return e;
+  expand_batch_kernel<<<count, 256, 0, stream>>>(d_in, d_prob, count);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned), stream);
+  if (e != cudaSuccess) return e;
+  if (total_chunks > 0) {
+    const bool c32 = precision == kPrecC32;
+    const int esz = c32 ? (int)sizeof(float2) : (int)sizeof(double2);
+    const int area = warp_area_elems(n_max > 0 ? n_max : 1, n_max > 0 ? n_max : 1, esz);
+    const size_t smem = (size_t)warps * area * (c32 ? sizeof(float2) : sizeof(double2));
+    int per_sm = 1;
+    if (c32) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lhaf_batch_kernel<float2>,
+                                                    32 * warps, smem);
+    } else {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lhaf_batch_kernel<double2>,
+                                                    32 * warps, smem);
+    }
+    if (per_sm < 1) per_sm = 1;
+    unsigned blocks = (unsigned)(per_sm * dev.sm_count);
+    const unsigned need = (total_chunks + warps - 1) / warps;
+    if (blocks > need) blocks = need;
+    if (c32) {
+      lhaf_batch_kernel<float2><<<blocks, 32 * warps, smem, stream>>>(
+          d_prob, count, total_chunks, area, d_counter, d_partials);
+    } else {
+      lhaf_batch_kernel<double2><<<blocks, 32 * warps, smem, stream>>>(
+          d_prob, count, total_chunks, area, d_counter, d_partials);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  lhaf_batch_finalize_kernel<<<(count + 127) / 128, 128, 0, stream>>>(d_prob, count, d_partials,
+                                                                      d_out);
+  return cudaGetLastError();
 }
 
 }  // namespace gbsh

@@ -59,4 +59,14 @@ cudaError_t launch_subset_terms(const LhafPlan& plan, const double2* base, int l
 cudaError_t launch_visit_count(const LhafPlan& plan, unsigned* counts, void* ws,
                                cudaStream_t stream);
 
+// Batched evaluation: warps per CTA that fit a problem of n_max pairs (0 if none fit).
+int batch_warps_for(int n_max, int precision, const DeviceInfo& dev, int warps_pref);
+
+// Expands, evaluates and reduces `count` problems. d_in/d_prob: device tables (problem
+// order = chunk order, largest first); d_out: 3 doubles per problem (re, im, sum |p_Z|).
+cudaError_t launch_batch(const BatchInput* d_in, const BatchProblem* d_prob, int count,
+                         unsigned total_chunks, int n_max, int precision, int warps,
+                         unsigned* d_counter, double* d_partials, double* d_out,
+                         cudaStream_t stream);
+
 }  // namespace gbsh
