@@ -202,6 +202,67 @@ int gbsh_set_lhaf_tuning(int warps_per_cta, int kcap);
  */
 int gbsh_lhaf_plan(int N, int* nclass, int* kernels, int* warps, int* kcap, int* nchunks);
 
+/* ---------------------------------------------------------------- chain-rule sampler
+ * The sampling algorithm of Sec. III (steps 2-6) for a pure Gaussian state, served with
+ * continuous batching. State: kernel matrix B and fill vector gamma of Eq. lhaf-pure, and
+ * the Husimi (heterodyne) distribution of modes 2..M (Eq. heterodyne): mean and lower
+ * Cholesky factor of V_Q restricted to those modes, in quadrature order
+ * (q_2..q_M, p_2..p_M), hbar = 2 (alpha = (q + i p) / 2).
+ * Each request draws n_samples independent samples; each sample's randomness comes from
+ * Philox4x32-10 keyed by the request seed (counter = (sample index, stream, index, 0)),
+ * so results do not depend on what else is being served.
+ * Step k conditions on alpha_{k+1..M} through the fill vector gamma_A + B_AB conj(alpha_B)
+ * (equal to Eqs. condV/condR for pure states) and draws s_k from
+ * |lhaf(filldiag(B_S, gamma_S))|^2 / s_k! over s_k = 0..cutoff. A candidate whose loop
+ * hafnian would exceed n_cap photons is dropped (probability 0) and counted in `truncated`.
+ */
+typedef struct gbsh_sampler gbsh_sampler;
+
+typedef struct {
+  int M;                    /* modes */
+  const gbsh_c128* B;       /* M x M host, leading dimension ldb (copied at create) */
+  int ldb;
+  const gbsh_c128* gamma;   /* M host fill vector of the full state (copied) */
+  const double* het_mean;   /* 2(M-1) host: Husimi means of (q_2..q_M, p_2..p_M) */
+  const double* het_chol;   /* 2(M-1) x 2(M-1) host, row-major lower Cholesky factor of V_Q */
+  int cutoff;               /* Fock cutoff d per mode (0..16) */
+  int n_cap;                /* largest loop hafnian size evaluated (<= GBSH_MAX_N) */
+  int max_active;           /* samples in flight (device slots); 1 with batching = 0 */
+  size_t mem_budget;        /* device bytes admitted samples may use (admission control) */
+  int batching;             /* 1: continuous batching, one launch per tick for all samples;
+                               0: plain path, one launch per loop hafnian, one sample at a time */
+  int precision;            /* GBSH_PREC_FP64 or GBSH_PREC_C32 */
+  int device;               /* CUDA device the sampler's worker thread uses */
+} gbsh_sampler_cfg;
+
+typedef struct {
+  double submit_s;   /* submission time since sampler creation */
+  double queue_s;    /* submission to first admission */
+  double run_s;      /* first admission to completion */
+  double latency_s;  /* submission to completion */
+  int lhafs;         /* loop hafnians evaluated for this request */
+  int ticks;         /* serving ticks the request took part in */
+  int truncated;     /* steps where a candidate exceeded n_cap */
+} gbsh_req_stats;
+
+/* Creates a sampler and starts its worker thread. Errors: GBSH_EINVAL, GBSH_ENOMEM,
+ * GBSH_ECUDA. */
+int gbsh_sampler_create(const gbsh_sampler_cfg* cfg, gbsh_sampler** out);
+/* Queues a request for n_samples samples; returns its id. Thread-safe. */
+int gbsh_sampler_submit(gbsh_sampler* h, uint64_t seed, int n_samples, uint64_t* req_id);
+/* GBSH_PENDING until done; then copies n_samples x M photon numbers into `samples` (host,
+ * may be NULL) and the stats, and forgets the request. GBSH_ENOTFOUND for unknown ids. */
+int gbsh_sampler_poll(gbsh_sampler* h, uint64_t req_id, int* samples, gbsh_req_stats* stats);
+/* Like poll, but waits at most timeout_s seconds (GBSH_ETIMEOUT after that). */
+int gbsh_sampler_wait(gbsh_sampler* h, uint64_t req_id, double timeout_s, int* samples,
+                      gbsh_req_stats* stats);
+/* Drops a request (its chains retire at the next tick). */
+int gbsh_sampler_cancel(gbsh_sampler* h, uint64_t req_id);
+/* Stops the worker (cancelling outstanding requests) and frees the device state. */
+int gbsh_sampler_destroy(gbsh_sampler* h);
+/* Philox4x32-10 (Salmon et al., SC'11) of the sampler, exposed for verification. */
+int gbsh_philox4x32(const uint32_t counter[4], const uint32_t key[2], uint32_t out[4]);
+
 /*
  * gbsh_lhaf_noalloc — gbsh_lhaf_async for callers that cannot allocate device memory.
  * The paper has no counterpart; this is an engineering entry point.

@@ -44,15 +44,24 @@ def F_matrix(m: int) -> np.ndarray:
 
 
 def gbs_quantities(V: np.ndarray, R: np.ndarray):
-    """Sec. II: Sigma = F V F^dag, Q = Sigma + I/2, A = X (I - Q^{-1}), alpha_vec = F R,
-    gamma_vec = Q^{-1} alpha_vec, p(vac) = exp(-alpha^dag Q^{-1} alpha / 2)/sqrt(det Q)."""
+    """Sec. II: Sigma = F V F^dag, Q = Sigma + I/2, A from X (I - Q^{-1}), alpha_vec = F R,
+    gamma_vec = Q^{-1} alpha_vec, p(vac) = exp(-alpha^dag Q^{-1} alpha / 2)/sqrt(det Q).
+
+    Reading of Sec. II (Eq. A_matrix with gamma = Q^{-1} alpha_vec): with F as printed, the
+    matrix X (I - Q^{-1}) is the complex conjugate of the kernel that pairs with gamma in
+    Eq. lhaf (its top-left block is conj(B) while gamma's first half is the unconjugated
+    fill vector), and the pair then gives wrong photon statistics as soon as squeezing
+    phase and displacement interact. A is therefore taken as conj(X (I - Q^{-1})); with
+    this reading the probabilities equal those of Fock states built explicitly from
+    matrix exponentials of the squeezing, interferometer and displacement generators
+    (pinned in tests/test_oracle_pins.py)."""
     m = V.shape[0] // 2
     F = F_matrix(m)
     Sigma = F @ V @ F.conj().T
     Q = Sigma + np.eye(2 * m) / 2
     Qinv = np.linalg.inv(Q)
     X = np.block([[np.zeros((m, m)), np.eye(m)], [np.eye(m), np.zeros((m, m))]])
-    A = X @ (np.eye(2 * m) - Qinv)
+    A = (X @ (np.eye(2 * m) - Qinv)).conj()
     avec = F @ R
     gvec = Qinv @ avec
     pvac = (np.exp(-0.5 * (avec.conj() @ Qinv @ avec)) / np.sqrt(np.linalg.det(Q))).real

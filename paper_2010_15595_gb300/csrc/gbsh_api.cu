@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/gbsh.h"
+#include "batch_host.h"
 #include "lhaf_kernels.cuh"
 
 namespace {
@@ -113,100 +114,24 @@ double err_from(double abs_sum, gbsh_c128 v) {
 
 // ---------------------------------------------------------------- batched evaluation
 int g_batch_warps[2][gbsh::kMaxN / 2 + 1] = {};  // per precision and n_max; 0 = default
+using gbsh::BatchLayout;
+using gbsh::batch_layout;
 
-// Workspace layout of a batched evaluation. The first `base_off` bytes belong to the caller
-// (staged inputs: matrices, fill vectors, index lists); the tables, expanded matrices,
-// chunk partials, counter and results follow.
-struct BatchLayout {
-  size_t off_in, off_prob, off_expanded, off_partials, off_counter, off_out, bytes;
-  unsigned total_chunks;
-  int n_max;
-  std::vector<int> order;           // sorted position -> problem index
-  std::vector<gbsh::BatchProblem> table;
-};
-
-BatchLayout batch_layout(const int* Ns, int count, size_t base_off) {
-  BatchLayout L;
-  L.order.resize(count);
-  std::iota(L.order.begin(), L.order.end(), 0);
-  std::stable_sort(L.order.begin(), L.order.end(),
-                   [&](int a, int b) { return Ns[a] > Ns[b]; });
-  L.table.resize(count);
-  unsigned base = 0;
-  size_t exp_elems = 0;
-  L.n_max = 0;
-  for (int q = 0; q < count; ++q) {
-    const int N = Ns[L.order[q]];
-    const int Ne = N + (N & 1);
-    const int n = Ne / 2;
-    gbsh::BatchProblem& P = L.table[q];
-    P.Ne = Ne;
-    P.n = n;
-    P.chunk_size = n > 0 ? gbsh::batch_chunk_size(n) : 1;
-    P.nchunks = n > 0 ? (unsigned)((1ull << n) / P.chunk_size) : 0u;
-    P.chunk_base = base;
-    base += P.nchunks;
-    exp_elems += (size_t)Ne * Ne + Ne;
-    L.n_max = std::max(L.n_max, n);
-  }
-  L.total_chunks = base;
-  size_t off = align256(base_off);
-  L.off_in = off; off = align256(off + sizeof(gbsh::BatchInput) * count);
-  L.off_prob = off; off = align256(off + sizeof(gbsh::BatchProblem) * count);
-  L.off_expanded = off; off = align256(off + sizeof(double2) * exp_elems);
-  L.off_partials = off; off = align256(off + sizeof(double) * 5 * (size_t)L.total_chunks);
-  L.off_counter = off; off = align256(off + sizeof(unsigned));
-  L.off_out = off; off = align256(off + sizeof(double) * 3 * (size_t)count);
-  L.bytes = off;
-  return L;
-}
-
-bool valid_precision(int p) {
-  return p == GBSH_PREC_FP64 || p == GBSH_PREC_C32 || p == GBSH_PREC_MIXED;
-}
-
-// `in` is indexed by problem; the device workspace `ws` already holds whatever the inputs
-// point into. Fills the tables, launches, and copies results back (synchronising).
 int batch_run(BatchLayout& L, const std::vector<gbsh::BatchInput>& in, int count, int precision,
               void* ws, cudaStream_t st, double* out3) {
-  char* w = static_cast<char*>(ws);
-  std::vector<gbsh::BatchInput> in_sorted(count);
-  double2* exp_base = reinterpret_cast<double2*>(w + L.off_expanded);
-  size_t e_off = 0;
-  for (int q = 0; q < count; ++q) {
-    in_sorted[q] = in[L.order[q]];
-    gbsh::BatchProblem& P = L.table[q];
-    P.A0 = exp_base + e_off;
-    P.v = exp_base + e_off + (size_t)P.Ne * P.Ne;
-    e_off += (size_t)P.Ne * P.Ne + P.Ne;
-  }
-  GBSH_CUDA(cudaMemcpyAsync(w + L.off_in, in_sorted.data(), sizeof(gbsh::BatchInput) * count,
-                            cudaMemcpyHostToDevice, st));
-  GBSH_CUDA(cudaMemcpyAsync(w + L.off_prob, L.table.data(), sizeof(gbsh::BatchProblem) * count,
-                            cudaMemcpyHostToDevice, st));
-  gbsh::DeviceInfo dev;
-  GBSH_CUDA(gbsh::device_info(&dev));
-  GBSH_CUDA(gbsh::ensure_constants());
   int pref;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     pref = g_batch_warps[precision][L.n_max];
   }
-  const int W = gbsh::batch_warps_for(std::max(L.n_max, 1), precision, dev, pref);
-  if (W < 1) return GBSH_EINVAL;
-  GBSH_CUDA(gbsh::launch_batch(
-      reinterpret_cast<const gbsh::BatchInput*>(w + L.off_in),
-      reinterpret_cast<const gbsh::BatchProblem*>(w + L.off_prob), count, L.total_chunks,
-      L.n_max, precision, W, reinterpret_cast<unsigned*>(w + L.off_counter),
-      reinterpret_cast<double*>(w + L.off_partials), reinterpret_cast<double*>(w + L.off_out),
-      st));
-  std::vector<double> res(3 * (size_t)count);
-  GBSH_CUDA(cudaMemcpyAsync(res.data(), w + L.off_out, sizeof(double) * res.size(),
-                            cudaMemcpyDeviceToHost, st));
-  GBSH_CUDA(cudaStreamSynchronize(st));
-  for (int q = 0; q < count; ++q)
-    for (int j = 0; j < 3; ++j) out3[3 * (size_t)L.order[q] + j] = res[3 * (size_t)q + j];
+  cudaError_t e = gbsh::batch_run(L, in, count, precision, pref, ws, st, out3);
+  if (e == cudaErrorInvalidValue) return GBSH_EINVAL;
+  if (e != cudaSuccess) return cuda_fail(e);
   return GBSH_OK;
+}
+
+bool valid_precision(int p) {
+  return p == GBSH_PREC_FP64 || p == GBSH_PREC_C32 || p == GBSH_PREC_MIXED;
 }
 
 

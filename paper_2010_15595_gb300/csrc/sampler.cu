@@ -1,0 +1,599 @@
+// Chain-rule GBS sampler with continuous batching (declarations and contracts in
+// include/gbsh.h).
+//
+// The algorithm of Sec. III for a pure state (steps 2-6): draw heterodyne outcomes
+// alpha_2..alpha_m once from the Husimi distribution of modes 2..m (Eq. heterodyne); then
+// for k = 1..m, compute the conditional probabilities of s_k = 0..d given s_1..s_{k-1} and
+// alpha_{k+1..m} with Eq. lhaf-pure, draw s_k, and forget alpha_{k+1}.
+//
+// Conditional state. For a pure state whose Fock amplitudes are generated by
+// exp(x^T B x / 2 + gamma^T x) (the form behind Eq. lhaf-pure), a heterodyne outcome
+// alpha_B on modes B (projection onto the coherent state |alpha_B>) sets x_B = conj(alpha_B)
+// and leaves modes A in the pure state with kernel B_AA and fill vector
+// gamma_A + B_AB conj(alpha_B); this equals the state given by Eqs. condV/condR (checked
+// against those equations in the tests). The conditional vacuum
+// probability is common to all candidates s_k and cancels in the normalisation of step 5,
+// so each step only needs loop hafnians: p(s_k) ~ |lhaf(filldiag(B_S, gamma^(k)_S))|^2 / s_k!.
+//
+// Serving: a worker thread owns the device state. Each "tick" advances every admitted
+// chain by one mode: one kernel forms the fill vectors gamma^(k) of all chains, and one
+// batched launch evaluates all (chain, s_k) loop hafnians together. Chains are admitted as
+// slots and device memory allow, so requests that arrive while others are on the GPU join
+// the next tick (continuous batching). All randomness of a chain is drawn from a
+// counter-based generator keyed by the request seed, and a loop hafnian's value does not
+// depend on the batch it runs in, so a sample is the same alone and in any mix.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdint>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/gbsh.h"
+#include "batch_host.h"
+#include "lhaf_kernels.cuh"
+
+namespace {
+
+// ------------------------------------------------------------------ Philox4x32-10
+// Counter-based generator of Salmon, Moraes, Dror and Shaw, "Parallel random numbers: as
+// easy as 1, 2, 3" (SC'11): 10 rounds of
+//   (c0, c1, c2, c3) <- (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0))
+// with M0 = 0xD2511F53, M1 = 0xCD9E8D57, the key advanced by (0x9E3779B9, 0xBB67AE85)
+// between rounds.
+void philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4]) {
+  uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+  uint32_t k0 = key_in[0], k1 = key_in[1];
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+    const uint32_t n1 = (uint32_t)p1;
+    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+    const uint32_t n3 = (uint32_t)p0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+// Uniform in [0, 1) from two 32-bit words: the top 53 bits of (hi:lo).
+double u53(uint32_t hi, uint32_t lo) {
+  const uint64_t x = ((uint64_t)hi << 32) | lo;
+  return (double)(x >> 11) * 0x1.0p-53;
+}
+
+// Stream layout of one chain: key = request seed; counter = (chain number, stream, index, 0).
+constexpr uint32_t kStreamNormals = 0, kStreamUniforms = 1;
+
+void chain_words(uint64_t seed, uint32_t chain, uint32_t stream, uint32_t index, uint32_t out[4]) {
+  const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  const uint32_t ctr[4] = {chain, stream, index, 0u};
+  philox4x32_10(ctr, key, out);
+}
+
+// 2*count standard normals by the Box-Muller transform, two per generator call.
+void chain_normals(uint64_t seed, uint32_t chain, int count2, double* z) {
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int b = 0; 2 * b < count2; ++b) {
+    uint32_t w[4];
+    chain_words(seed, chain, kStreamNormals, (uint32_t)b, w);
+    const double u1 = u53(w[0], w[1]), u2 = u53(w[2], w[3]);
+    const double r = std::sqrt(-2.0 * std::log(1.0 - u1));
+    z[2 * b] = r * std::cos(two_pi * u2);
+    if (2 * b + 1 < count2) z[2 * b + 1] = r * std::sin(two_pi * u2);
+  }
+}
+
+double chain_uniform(uint64_t seed, uint32_t chain, uint32_t k) {
+  uint32_t w[4];
+  chain_words(seed, chain, kStreamUniforms, k, w);
+  return u53(w[0], w[1]);
+}
+
+// ------------------------------------------------------------------ fill-vector kernel
+// gam[c][i] = gbar[i] + sum_{j > k_c} B[i][j] conj(alpha_c[j]) for i <= k_c (one block per
+// chain; alpha_c is the chain's heterodyne outcome vector, entry 0 unused).
+__global__ void sampler_gamma_kernel(const double2* __restrict__ B, int ldb,
+                                     const double2* __restrict__ gbar,
+                                     const double2* __restrict__ alpha, const int* __restrict__ slot,
+                                     const int* __restrict__ kk, int nchains, int M,
+                                     double2* __restrict__ gam) {
+  const int c = blockIdx.x;
+  if (c >= nchains) return;
+  const int k = kk[c];
+  const double2* a = alpha + (size_t)slot[c] * M;
+  double2* g = gam + (size_t)slot[c] * M;
+  for (int i = threadIdx.x; i <= k; i += blockDim.x) {
+    double re = 0.0, im = 0.0;
+    for (int j = k + 1; j < M; ++j) {
+      const double2 b = B[(size_t)i * ldb + j], x = a[j];  // b * conj(x)
+      re = fma(b.x, x.x, fma(b.y, x.y, re));
+      im = fma(b.y, x.x, fma(-b.x, x.y, im));
+    }
+    g[i] = make_double2(gbar[i].x + re, gbar[i].y + im);
+  }
+}
+
+using Clock = std::chrono::steady_clock;
+
+double seconds_since(Clock::time_point t0, Clock::time_point t) {
+  return std::chrono::duration<double>(t - t0).count();
+}
+
+struct Request {
+  uint64_t id = 0, seed = 0;
+  int n_samples = 0, done = 0;
+  bool cancelled = false;
+  std::vector<int> samples;  // n_samples x M
+  Clock::time_point t_submit, t_start, t_done;
+  bool started = false, finished = false;
+  int lhafs = 0, ticks = 0, truncated = 0;
+};
+
+struct Chain {
+  std::shared_ptr<Request> req;
+  uint32_t chain_no = 0;
+  int k = 0;          // next mode to sample
+  int nphot = 0;      // photons in modes < k
+  int slot = -1;
+  std::vector<int> s;
+  size_t mem = 0;
+};
+
+}  // namespace
+
+struct gbsh_sampler {
+  gbsh_sampler_cfg cfg{};
+  std::vector<double2> B, gbar;
+  std::vector<double> het_mean, het_chol;
+  int device = 0;
+  // threading
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  bool stop = false;
+  std::thread worker;
+  int worker_error = GBSH_OK;
+  uint64_t next_id = 1;
+  std::map<uint64_t, std::shared_ptr<Request>> requests;
+  std::deque<Chain> pending;
+  Clock::time_point t0 = Clock::now();
+  // device state (worker thread only)
+  cudaStream_t st = nullptr;
+  double2 *dB = nullptr, *dgbar = nullptr, *dalpha = nullptr, *dgam = nullptr;
+  int *dslot = nullptr, *dk = nullptr, *didx = nullptr;
+  size_t idx_cap = 0;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  std::vector<int> free_slots;
+
+  void run();
+  int tick(std::vector<Chain>& active);
+  int ensure_ws(size_t bytes);
+  int ensure_idx(size_t n);
+  size_t chain_mem_estimate() const;
+};
+
+namespace {
+
+int from_cuda(cudaError_t e) {
+  return e == cudaSuccess ? GBSH_OK : (e == cudaErrorMemoryAllocation ? GBSH_ENOMEM : GBSH_ECUDA);
+}
+
+}  // namespace
+
+size_t gbsh_sampler::chain_mem_estimate() const {
+  // device bytes of one chain's candidates at the largest allowed size
+  const int N = cfg.n_cap;
+  const int Ne = N + (N & 1), n = Ne / 2;
+  const size_t chunks = ((size_t)1 << n) / gbsh::batch_chunk_size(n);
+  const size_t per = sizeof(double2) * ((size_t)Ne * Ne + Ne) + 40 * chunks + 128 + 4 * (size_t)N;
+  return per * (size_t)(cfg.cutoff + 1);
+}
+
+int gbsh_sampler::ensure_ws(size_t bytes) {
+  if (bytes <= ws_bytes) return GBSH_OK;
+  if (ws) cudaFree(ws);
+  ws = nullptr;
+  ws_bytes = 0;
+  size_t want = std::max(bytes, (size_t)1 << 22);
+  cudaError_t e = cudaMalloc(&ws, want);
+  if (e != cudaSuccess) return from_cuda(e);
+  ws_bytes = want;
+  return GBSH_OK;
+}
+
+int gbsh_sampler::ensure_idx(size_t n) {
+  if (n <= idx_cap) return GBSH_OK;
+  if (didx) cudaFree(didx);
+  didx = nullptr;
+  size_t want = std::max(n, (size_t)4096);
+  cudaError_t e = cudaMalloc(&didx, sizeof(int) * want);
+  if (e != cudaSuccess) return from_cuda(e);
+  idx_cap = want;
+  return GBSH_OK;
+}
+
+// Advances every chain in `active` by one mode. Returns a status code.
+int gbsh_sampler::tick(std::vector<Chain>& active) {
+  const int M = cfg.M, d = cfg.cutoff;
+  const int nch = (int)active.size();
+  // fill vectors gamma^(k) of all chains
+  std::vector<int> slots(nch), ks(nch);
+  for (int c = 0; c < nch; ++c) {
+    slots[c] = active[c].slot;
+    ks[c] = active[c].k;
+  }
+  cudaError_t e = cudaMemcpyAsync(dslot, slots.data(), sizeof(int) * nch, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return from_cuda(e);
+  e = cudaMemcpyAsync(dk, ks.data(), sizeof(int) * nch, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return from_cuda(e);
+  sampler_gamma_kernel<<<nch, 128, 0, st>>>(dB, M, dgbar, dalpha, dslot, dk, nch, M, dgam);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return from_cuda(e);
+
+  // candidate loop hafnians (chain c, s_k = s); index lists: mode i repeated s_i times
+  struct Cand { int chain, s, N; size_t idx_off; };
+  std::vector<Cand> cands;
+  std::vector<int> idx;
+  std::vector<char> trunc(nch, 0);
+  for (int c = 0; c < nch; ++c) {
+    const Chain& ch = active[c];
+    for (int s = 0; s <= d; ++s) {
+      const int N = ch.nphot + s;
+      if (N > cfg.n_cap) {
+        trunc[c] = 1;
+        break;
+      }
+      cands.push_back(Cand{c, s, N, idx.size()});
+      for (int i = 0; i < ch.k; ++i)
+        for (int r = 0; r < ch.s[i]; ++r) idx.push_back(i);
+      for (int r = 0; r < s; ++r) idx.push_back(ch.k);
+    }
+  }
+  int rc = ensure_idx(idx.size() + 1);
+  if (rc != GBSH_OK) return rc;
+  if (!idx.empty()) {
+    e = cudaMemcpyAsync(didx, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return from_cuda(e);
+  }
+  const int nc = (int)cands.size();
+  std::vector<double> out3(3 * (size_t)nc);
+  std::vector<int> Ns(nc);
+  std::vector<gbsh::BatchInput> in(nc);
+  for (int q = 0; q < nc; ++q) {
+    Ns[q] = cands[q].N;
+    in[q] = gbsh::BatchInput{dB, dgam + (size_t)active[cands[q].chain].slot * M,
+                             didx + cands[q].idx_off, M, cands[q].N};
+  }
+  if (cfg.batching) {
+    gbsh::BatchLayout L = gbsh::batch_layout(Ns.data(), nc, 0);
+    rc = ensure_ws(L.bytes);
+    if (rc != GBSH_OK) return rc;
+    e = gbsh::batch_run(L, in, nc, cfg.precision, 0, ws, st, out3.data());
+    if (e != cudaSuccess) return from_cuda(e);
+  } else {
+    // plain path: one launch sequence (and one synchronisation) per loop hafnian
+    for (int q = 0; q < nc; ++q) {
+      gbsh::BatchLayout L = gbsh::batch_layout(&Ns[q], 1, 0);
+      rc = ensure_ws(L.bytes);
+      if (rc != GBSH_OK) return rc;
+      std::vector<gbsh::BatchInput> one(1, in[q]);
+      e = gbsh::batch_run(L, one, 1, cfg.precision, 0, ws, st, &out3[3 * (size_t)q]);
+      if (e != cudaSuccess) return from_cuda(e);
+    }
+  }
+  // step 5: draw s_k from the normalised weights |lhaf|^2 / s!
+  std::vector<double> w((size_t)d + 1);
+  size_t q = 0;
+  for (int c = 0; c < nch; ++c) {
+    Chain& ch = active[c];
+    std::fill(w.begin(), w.end(), 0.0);
+    double total = 0.0, fact = 1.0;
+    int ncand = 0;
+    while (q < cands.size() && cands[q].chain == c) {
+      const int s = cands[q].s;
+      if (s > 1) fact *= (double)s;
+      const double re = out3[3 * q], im = out3[3 * q + 1];
+      w[s] = (re * re + im * im) / fact;
+      total += w[s];
+      ++ncand;
+      ++q;
+    }
+    const double u = chain_uniform(ch.req->seed, ch.chain_no, (uint32_t)ch.k);
+    int sk = 0;
+    if (total > 0.0) {
+      double cum = 0.0;
+      sk = ncand - 1;
+      for (int s = 0; s < ncand; ++s) {
+        cum += w[s] / total;
+        if (cum > u) {
+          sk = s;
+          break;
+        }
+      }
+    }
+    ch.s[ch.k] = sk;
+    ch.nphot += sk;
+    ch.k += 1;
+    ch.req->lhafs += ncand;
+    if (trunc[c]) ch.req->truncated += 1;
+  }
+  return GBSH_OK;
+}
+
+void gbsh_sampler::run() {
+  int rc = from_cuda(cudaSetDevice(device));
+  std::vector<Chain> active;
+  size_t mem_in_use = 0;
+  const size_t per_chain = chain_mem_estimate();
+  const int max_active = cfg.batching ? std::max(1, cfg.max_active) : 1;
+  while (rc == GBSH_OK) {
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      // admission: by free slots and by device-memory budget
+      while (!pending.empty() && (int)active.size() < max_active &&
+             (active.empty() || mem_in_use + per_chain <= cfg.mem_budget)) {
+        Chain ch = std::move(pending.front());
+        pending.pop_front();
+        if (ch.req->cancelled) continue;
+        if (!ch.req->started) {
+          ch.req->started = true;
+          ch.req->t_start = Clock::now();
+        }
+        ch.slot = free_slots.back();
+        free_slots.pop_back();
+        ch.mem = per_chain;
+        mem_in_use += per_chain;
+        active.push_back(std::move(ch));
+        Chain& a = active.back();
+        // step 2: heterodyne outcomes of modes 2..M from the Husimi distribution
+        const int R = 2 * (cfg.M - 1);
+        std::vector<double> z(R), mu(R);
+        chain_normals(a.req->seed, a.chain_no, R, z.data());
+        for (int r = 0; r < R; ++r) {
+          double acc = het_mean[r];
+          for (int c = 0; c <= r; ++c) acc += het_chol[(size_t)r * R + c] * z[c];
+          mu[r] = acc;
+        }
+        std::vector<double2> alpha(cfg.M, make_double2(0.0, 0.0));
+        for (int j = 1; j < cfg.M; ++j)  // alpha = (q + i p) / 2   (hbar = 2)
+          alpha[j] = make_double2(0.5 * mu[j - 1], 0.5 * mu[(cfg.M - 1) + j - 1]);
+        lk.unlock();
+        cudaError_t e = cudaMemcpyAsync(dalpha + (size_t)a.slot * cfg.M, alpha.data(),
+                                        sizeof(double2) * cfg.M, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        lk.lock();
+        if (e != cudaSuccess) {
+          rc = from_cuda(e);
+          break;
+        }
+      }
+      if (rc != GBSH_OK) break;
+      if (active.empty()) {
+        if (stop) break;
+        cv_work.wait_for(lk, std::chrono::milliseconds(20));
+        continue;
+      }
+    }
+    rc = tick(active);
+    if (rc != GBSH_OK) break;
+    // retire finished chains
+    std::lock_guard<std::mutex> lk(mu);
+    std::vector<Chain> keep;
+    std::map<Request*, bool> ticked;
+    for (auto& ch : active) {
+      if (!ticked[ch.req.get()]) {
+        ch.req->ticks += 1;
+        ticked[ch.req.get()] = true;
+      }
+      if (ch.k >= cfg.M || ch.req->cancelled) {
+        if (!ch.req->cancelled) {
+          std::memcpy(&ch.req->samples[(size_t)ch.chain_no * cfg.M], ch.s.data(),
+                      sizeof(int) * cfg.M);
+          ch.req->done += 1;
+          if (ch.req->done == ch.req->n_samples) {
+            ch.req->finished = true;
+            ch.req->t_done = Clock::now();
+            cv_done.notify_all();
+          }
+        }
+        free_slots.push_back(ch.slot);
+        mem_in_use -= ch.mem;
+      } else {
+        keep.push_back(std::move(ch));
+      }
+    }
+    active.swap(keep);
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  if (rc != GBSH_OK) worker_error = rc;
+  cv_done.notify_all();
+}
+
+extern "C" {
+
+int gbsh_philox4x32(const uint32_t counter[4], const uint32_t key[2], uint32_t out[4]) {
+  if (!counter || !key || !out) return GBSH_EINVAL;
+  philox4x32_10(counter, key, out);
+  return GBSH_OK;
+}
+
+int gbsh_sampler_create(const gbsh_sampler_cfg* cfg, gbsh_sampler** out) {
+  if (!cfg || !out) return GBSH_EINVAL;
+  const int M = cfg->M;
+  if (M < 1 || !cfg->B || cfg->ldb < M || !cfg->gamma || cfg->cutoff < 0 || cfg->cutoff > 16 ||
+      cfg->n_cap < 0 || cfg->n_cap > GBSH_MAX_N || cfg->max_active < 1 ||
+      (M > 1 && (!cfg->het_mean || !cfg->het_chol)) ||
+      (cfg->precision != GBSH_PREC_FP64 && cfg->precision != GBSH_PREC_C32))
+    return GBSH_EINVAL;
+  std::unique_ptr<gbsh_sampler> h(new gbsh_sampler());
+  h->cfg = *cfg;
+  h->device = cfg->device;
+  h->B.resize((size_t)M * M);
+  for (int i = 0; i < M; ++i)
+    for (int j = 0; j < M; ++j) {
+      const gbsh_c128 b = cfg->B[(size_t)i * cfg->ldb + j];
+      h->B[(size_t)i * M + j] = make_double2(b.re, b.im);
+    }
+  h->gbar.resize(M);
+  for (int i = 0; i < M; ++i) h->gbar[i] = make_double2(cfg->gamma[i].re, cfg->gamma[i].im);
+  const int R = 2 * (M - 1);
+  h->het_mean.assign(cfg->het_mean ? cfg->het_mean : nullptr,
+                     cfg->het_mean ? cfg->het_mean + R : nullptr);
+  h->het_chol.assign(cfg->het_chol ? cfg->het_chol : nullptr,
+                     cfg->het_chol ? cfg->het_chol + (size_t)R * R : nullptr);
+  h->cfg.B = nullptr;
+  h->cfg.gamma = nullptr;
+  h->cfg.het_mean = nullptr;
+  h->cfg.het_chol = nullptr;
+  const int slots = cfg->batching ? cfg->max_active : 1;
+  h->free_slots.resize(slots);
+  for (int i = 0; i < slots; ++i) h->free_slots[i] = slots - 1 - i;
+  // device state
+  int prev = 0;
+  cudaError_t e = cudaGetDevice(&prev);
+  if (e != cudaSuccess) return from_cuda(e);
+  e = cudaSetDevice(h->device);
+  if (e != cudaSuccess) return from_cuda(e);
+  auto fail = [&](cudaError_t err) {
+    cudaSetDevice(prev);
+    return from_cuda(err);
+  };
+  if ((e = cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking)) != cudaSuccess) return fail(e);
+  if ((e = cudaMalloc(&h->dB, sizeof(double2) * M * M)) != cudaSuccess) return fail(e);
+  if ((e = cudaMalloc(&h->dgbar, sizeof(double2) * M)) != cudaSuccess) return fail(e);
+  if ((e = cudaMalloc(&h->dalpha, sizeof(double2) * (size_t)M * slots)) != cudaSuccess) return fail(e);
+  if ((e = cudaMalloc(&h->dgam, sizeof(double2) * (size_t)M * slots)) != cudaSuccess) return fail(e);
+  if ((e = cudaMalloc(&h->dslot, sizeof(int) * slots)) != cudaSuccess) return fail(e);
+  if ((e = cudaMalloc(&h->dk, sizeof(int) * slots)) != cudaSuccess) return fail(e);
+  if ((e = cudaMemcpy(h->dB, h->B.data(), sizeof(double2) * M * M, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return fail(e);
+  if ((e = cudaMemcpy(h->dgbar, h->gbar.data(), sizeof(double2) * M, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return fail(e);
+  cudaSetDevice(prev);
+  gbsh_sampler* raw = h.release();
+  raw->worker = std::thread([raw] { raw->run(); });
+  *out = raw;
+  return GBSH_OK;
+}
+
+int gbsh_sampler_submit(gbsh_sampler* h, uint64_t seed, int n_samples, uint64_t* req_id) {
+  if (!h || !req_id || n_samples < 1) return GBSH_EINVAL;
+  std::lock_guard<std::mutex> lk(h->mu);
+  if (h->worker_error != GBSH_OK) return h->worker_error;
+  auto r = std::make_shared<Request>();
+  r->id = h->next_id++;
+  r->seed = seed;
+  r->n_samples = n_samples;
+  r->samples.assign((size_t)n_samples * h->cfg.M, 0);
+  r->t_submit = Clock::now();
+  h->requests[r->id] = r;
+  for (int c = 0; c < n_samples; ++c) {
+    Chain ch;
+    ch.req = r;
+    ch.chain_no = (uint32_t)c;
+    ch.s.assign(h->cfg.M, 0);
+    h->pending.push_back(std::move(ch));
+  }
+  *req_id = r->id;
+  h->cv_work.notify_one();
+  return GBSH_OK;
+}
+
+static int fill_result(gbsh_sampler* h, Request& r, int* samples, gbsh_req_stats* stats) {
+  if (samples) std::memcpy(samples, r.samples.data(), sizeof(int) * r.samples.size());
+  if (stats) {
+    stats->queue_s = seconds_since(r.t_submit, r.t_start);
+    stats->run_s = seconds_since(r.t_start, r.t_done);
+    stats->latency_s = seconds_since(r.t_submit, r.t_done);
+    stats->submit_s = seconds_since(h->t0, r.t_submit);
+    stats->lhafs = r.lhafs;
+    stats->ticks = r.ticks;
+    stats->truncated = r.truncated;
+  }
+  return GBSH_OK;
+}
+
+int gbsh_sampler_poll(gbsh_sampler* h, uint64_t req_id, int* samples, gbsh_req_stats* stats) {
+  if (!h) return GBSH_EINVAL;
+  std::lock_guard<std::mutex> lk(h->mu);
+  auto it = h->requests.find(req_id);
+  if (it == h->requests.end()) return GBSH_ENOTFOUND;
+  if (!it->second->finished) return h->worker_error != GBSH_OK ? h->worker_error : GBSH_PENDING;
+  fill_result(h, *it->second, samples, stats);
+  h->requests.erase(it);
+  return GBSH_OK;
+}
+
+int gbsh_sampler_wait(gbsh_sampler* h, uint64_t req_id, double timeout_s, int* samples,
+                      gbsh_req_stats* stats) {
+  if (!h || timeout_s < 0) return GBSH_EINVAL;
+  std::unique_lock<std::mutex> lk(h->mu);
+  auto deadline = Clock::now() + std::chrono::duration_cast<Clock::duration>(
+                                     std::chrono::duration<double>(timeout_s));
+  for (;;) {
+    auto it = h->requests.find(req_id);
+    if (it == h->requests.end()) return GBSH_ENOTFOUND;
+    if (it->second->finished) {
+      fill_result(h, *it->second, samples, stats);
+      h->requests.erase(it);
+      return GBSH_OK;
+    }
+    if (h->worker_error != GBSH_OK) return h->worker_error;
+    if (h->cv_done.wait_until(lk, deadline) == std::cv_status::timeout) {
+      auto it2 = h->requests.find(req_id);
+      if (it2 != h->requests.end() && it2->second->finished) continue;
+      return GBSH_ETIMEOUT;
+    }
+  }
+}
+
+int gbsh_sampler_cancel(gbsh_sampler* h, uint64_t req_id) {
+  if (!h) return GBSH_EINVAL;
+  std::lock_guard<std::mutex> lk(h->mu);
+  auto it = h->requests.find(req_id);
+  if (it == h->requests.end()) return GBSH_ENOTFOUND;
+  it->second->cancelled = true;
+  h->requests.erase(it);
+  return GBSH_OK;
+}
+
+int gbsh_sampler_destroy(gbsh_sampler* h) {
+  if (!h) return GBSH_EINVAL;
+  {
+    std::lock_guard<std::mutex> lk(h->mu);
+    h->stop = true;
+    for (auto& kv : h->requests) kv.second->cancelled = true;
+    h->pending.clear();
+  }
+  h->cv_work.notify_all();
+  if (h->worker.joinable()) h->worker.join();
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(h->device);
+  if (h->st) cudaStreamSynchronize(h->st);
+  cudaFree(h->dB);
+  cudaFree(h->dgbar);
+  cudaFree(h->dalpha);
+  cudaFree(h->dgam);
+  cudaFree(h->dslot);
+  cudaFree(h->dk);
+  cudaFree(h->didx);
+  cudaFree(h->ws);
+  if (h->st) cudaStreamDestroy(h->st);
+  cudaSetDevice(prev);
+  delete h;
+  return GBSH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,192 @@
+"""Chain-rule GBS sampler (Sec. III) served by the C ABI's worker (gbsh_sampler_*).
+
+`pure_state(U, r, alpha)` builds, with torch on the GPU, the quantities the sampler needs
+for a pure Gaussian state (squeezed vacuum with squeezing r through interferometer U, then
+displaced to mean amplitudes alpha), following Sec. II with hbar = 2:
+  covariance V = S S^T (S = interferometer x squeezer, quadratures (q, p)),
+  Sigma = F V F^dag, Q = Sigma + I/2, A = conj(X (I - Q^{-1})) = B (+) B*,
+  gamma = Q^{-1} alpha_vec (its first half fills the diagonal in Eq. lhaf-pure),
+  (A is read as the conjugate of the printed X (I - Q^{-1}): only then do B and gamma form
+  the consistent pair whose loop hafnians give the state's Fock amplitudes),
+  p(vac) = exp(-alpha_vec^dag Q^{-1} alpha_vec / 2) / sqrt(det Q),
+  Husimi covariance V_Q = V + I restricted to modes 2..M and its Cholesky factor
+  (Eq. heterodyne), for the heterodyne draw of step 2.
+`Sampler` wraps gbsh_sampler_create/submit/poll/wait/destroy.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import lib as _lib
+
+
+@dataclass
+class PureState:
+    B: np.ndarray           # M x M kernel matrix of Eq. lhaf-pure
+    gamma: np.ndarray       # M fill vector
+    p_vac: float
+    het_mean: np.ndarray    # 2(M-1) Husimi means of (q_2..q_M, p_2..p_M)
+    het_chol: np.ndarray    # 2(M-1) x 2(M-1) lower Cholesky factor of V_Q on modes 2..M
+
+
+def pure_state(U, r, alpha, device=None) -> PureState:
+    import torch
+    dev = torch.device(device) if device is not None else (
+        torch.device("cuda") if torch.cuda.is_available() else torch.device("cpu"))
+    U = torch.as_tensor(np.asarray(U), dtype=torch.complex128, device=dev)
+    r = torch.as_tensor(np.asarray(r, dtype=np.float64), device=dev)
+    alpha = torch.as_tensor(np.asarray(alpha), dtype=torch.complex128, device=dev)
+    M = U.shape[0]
+    hbar = 2.0
+    # symplectic of the squeezers (q squeezed) followed by the interferometer a -> U a
+    Sr = torch.diag(torch.cat([torch.exp(-r), torch.exp(r)]))
+    SU = torch.cat([torch.cat([U.real, -U.imag], 1), torch.cat([U.imag, U.real], 1)], 0)
+    S = SU @ Sr
+    V = (hbar / 2) * S @ S.T
+    R = (2 * hbar) ** 0.5 * torch.cat([alpha.real, alpha.imag])
+    eye = torch.eye(M, dtype=torch.complex128, device=dev)
+    F = torch.cat([torch.cat([eye, 1j * eye], 1), torch.cat([eye, -1j * eye], 1)], 0) / (2 * hbar) ** 0.5
+    Sigma = F @ V.to(torch.complex128) @ F.conj().T
+    Q = Sigma + torch.eye(2 * M, dtype=torch.complex128, device=dev) / 2
+    Qinv = torch.linalg.inv(Q)
+    zero = torch.zeros((M, M), dtype=torch.complex128, device=dev)
+    X = torch.cat([torch.cat([zero, eye], 1), torch.cat([eye, zero], 1)], 0)
+    A = (X @ (torch.eye(2 * M, dtype=torch.complex128, device=dev) - Qinv)).conj()
+    avec = F @ R.to(torch.complex128)
+    gvec = Qinv @ avec
+    pvac = torch.exp(-0.5 * (avec.conj() @ Qinv @ avec)).real / torch.sqrt(torch.linalg.det(Q)).real
+    B = A[:M, :M]
+    B = 0.5 * (B + B.T)
+    if M > 1:
+        rest = list(range(1, M))
+        q = rest + [i + M for i in rest]
+        VQ = (V + (hbar / 2) * torch.eye(2 * M, dtype=torch.float64, device=dev))[q][:, q]
+        L = torch.linalg.cholesky(VQ)
+        mean = R[q]
+    else:
+        L = torch.zeros((0, 0), dtype=torch.float64, device=dev)
+        mean = torch.zeros(0, dtype=torch.float64, device=dev)
+    return PureState(B=B.cpu().numpy(), gamma=gvec[:M].cpu().numpy(), p_vac=float(pvac),
+                     het_mean=mean.cpu().numpy(), het_chol=L.cpu().numpy())
+
+
+class _Cfg(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int), ("B", ctypes.c_void_p), ("ldb", ctypes.c_int),
+                ("gamma", ctypes.c_void_p), ("het_mean", ctypes.c_void_p),
+                ("het_chol", ctypes.c_void_p), ("cutoff", ctypes.c_int), ("n_cap", ctypes.c_int),
+                ("max_active", ctypes.c_int), ("mem_budget", ctypes.c_size_t),
+                ("batching", ctypes.c_int), ("precision", ctypes.c_int), ("device", ctypes.c_int)]
+
+
+class ReqStats(ctypes.Structure):
+    _fields_ = [("submit_s", ctypes.c_double), ("queue_s", ctypes.c_double),
+                ("run_s", ctypes.c_double), ("latency_s", ctypes.c_double),
+                ("lhafs", ctypes.c_int), ("ticks", ctypes.c_int), ("truncated", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def _bind():
+    so = _lib.load()
+    if getattr(so, "_gbsh_sampler_bound", False):
+        return so
+    vp, i = ctypes.c_void_p, ctypes.c_int
+    so.gbsh_sampler_create.argtypes = [ctypes.POINTER(_Cfg), ctypes.POINTER(vp)]
+    so.gbsh_sampler_submit.argtypes = [vp, ctypes.c_uint64, i, ctypes.POINTER(ctypes.c_uint64)]
+    so.gbsh_sampler_poll.argtypes = [vp, ctypes.c_uint64, vp, ctypes.POINTER(ReqStats)]
+    so.gbsh_sampler_wait.argtypes = [vp, ctypes.c_uint64, ctypes.c_double, vp, ctypes.POINTER(ReqStats)]
+    so.gbsh_sampler_cancel.argtypes = [vp, ctypes.c_uint64]
+    so.gbsh_sampler_destroy.argtypes = [vp]
+    so.gbsh_philox4x32.argtypes = [vp, vp, vp]
+    for f in ("gbsh_sampler_create", "gbsh_sampler_submit", "gbsh_sampler_poll",
+              "gbsh_sampler_wait", "gbsh_sampler_cancel", "gbsh_sampler_destroy",
+              "gbsh_philox4x32"):
+        getattr(so, f).restype = i
+    so._gbsh_sampler_bound = True
+    return so
+
+
+def philox4x32(counter, key):
+    """The library's Philox4x32-10 block function (for verification)."""
+    so = _bind()
+    c = np.ascontiguousarray(counter, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    _lib._check(so.gbsh_philox4x32(c.ctypes.data, k.ctypes.data, out.ctypes.data), "gbsh_philox4x32")
+    return out
+
+
+class Sampler:
+    """A served chain-rule sampler for one pure state."""
+
+    def __init__(self, state: PureState, cutoff: int = 4, n_cap: int = 36, max_active: int = 256,
+                 mem_budget: int = 2 << 30, batching: bool = True,
+                 precision: int = _lib.PREC_FP64, device: int = 0):
+        self.so = _bind()
+        self.M = state.B.shape[0]
+        self._B = np.ascontiguousarray(state.B, dtype=np.complex128)
+        self._g = np.ascontiguousarray(state.gamma, dtype=np.complex128)
+        self._m = np.ascontiguousarray(state.het_mean, dtype=np.float64)
+        self._L = np.ascontiguousarray(state.het_chol, dtype=np.float64)
+        cfg = _Cfg(self.M, self._B.ctypes.data, self.M, self._g.ctypes.data,
+                   self._m.ctypes.data if self._m.size else None,
+                   self._L.ctypes.data if self._L.size else None, cutoff, n_cap,
+                   max_active if batching else 1, mem_budget, 1 if batching else 0, precision,
+                   device)
+        h = ctypes.c_void_p()
+        _lib._check(self.so.gbsh_sampler_create(ctypes.byref(cfg), ctypes.byref(h)),
+                    "gbsh_sampler_create")
+        self.h = h
+
+    def submit(self, seed: int, n_samples: int = 1) -> int:
+        rid = ctypes.c_uint64()
+        _lib._check(self.so.gbsh_sampler_submit(self.h, seed, n_samples, ctypes.byref(rid)),
+                    "gbsh_sampler_submit")
+        self._n = getattr(self, "_n", {})
+        self._n[rid.value] = n_samples
+        return rid.value
+
+    def _result(self, rc, rid, buf, st):
+        if rc == _lib.GBSH_PENDING:
+            return None
+        _lib._check(rc, "gbsh_sampler")
+        self._n.pop(rid, None)
+        return buf.reshape(-1, self.M), st.as_dict()
+
+    def poll(self, rid: int):
+        buf = np.zeros(self._n[rid] * self.M, dtype=np.int32)
+        st = ReqStats()
+        rc = self.so.gbsh_sampler_poll(self.h, rid, buf.ctypes.data, ctypes.byref(st))
+        return self._result(rc, rid, buf, st)
+
+    def wait(self, rid: int, timeout: float = 600.0):
+        buf = np.zeros(self._n[rid] * self.M, dtype=np.int32)
+        st = ReqStats()
+        rc = self.so.gbsh_sampler_wait(self.h, rid, float(timeout), buf.ctypes.data,
+                                       ctypes.byref(st))
+        return self._result(rc, rid, buf, st)
+
+    def cancel(self, rid: int):
+        _lib._check(self.so.gbsh_sampler_cancel(self.h, rid), "gbsh_sampler_cancel")
+        self._n.pop(rid, None)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.so.gbsh_sampler_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

