@@ -265,6 +265,9 @@ def run_ours(args, rank, world, local_rank):
     batch = None
     if args.batch and rank == 0:
         batch = run_batch_workload(lib, workloads, workmodel, dev, stream)
+    serving = None
+    if args.serving and rank == 0:
+        serving = run_serving_workload(args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -297,6 +300,7 @@ def run_ours(args, rank, world, local_rank):
                        "err_est": kappa * 2.0 ** -53},
             "n50": n50,
             "batch": batch,
+            "serving": serving,
             "paper_context": "Fig. 3: N=40 in 44.9 s (23.3k subset-terms/s), N=50 in 2499 s "
                              "(13.4k/s), long double, 96 vCPUs @ 2.345 GHz",
         }
@@ -343,6 +347,62 @@ def run_batch_workload(lib, workloads, workmodel, dev, stream, count=4096):
     return res
 
 
+def run_serving_workload(args):
+    """Chain-rule sampler (Sec. III) on the serving state: M=100 modes, Haar U, r=0.8 on 25
+    input modes (mean ~20 photons), output displacement ~CN(0, 0.1^2), Fock cutoff 4, loop
+    hafnians up to N=36. Plain path (one launch per loop hafnian, one sample at a time) vs
+    the served path (continuous batching); Poisson arrivals at fixed multiples of the plain
+    throughput; latencies from submission to completion."""
+    import numpy as np
+    from paper_2010_15595_gb300 import sampler as S, workloads
+    U, r, alpha = workloads.serving_state()
+    st = S.pure_state(U, r, alpha)
+    res = {"workload": "chain-rule GBS sampler, M=100, r=0.8 on 25 modes, alpha~CN(0,0.1^2), "
+                       "cutoff 4, N<=36 (candidates above are dropped and counted)"}
+
+    def run_batch(smp, seeds):
+        t = time.perf_counter()
+        rids = [smp.submit(s_) for s_ in seeds]
+        out = [smp.wait(rr, timeout=900) for rr in rids]
+        return time.perf_counter() - t, out
+
+    with S.Sampler(st, cutoff=4, n_cap=36, batching=False) as plain:
+        dt, out = run_batch(plain, range(args.serve_plain))
+    plain_rate = args.serve_plain / dt
+    lat = [o[1]["latency_s"] for o in out]
+    res["plain"] = {"samples": args.serve_plain, "samples_per_s": plain_rate,
+                    "mean_photons": float(np.mean([o[0].sum() for o in out])),
+                    "note": "all submitted at t=0 (saturated)"}
+    with S.Sampler(st, cutoff=4, n_cap=36, max_active=args.serve_slots) as smp:
+        dt, out = run_batch(smp, range(1000, 1000 + args.serve_saturated))
+        res["served_saturated"] = {"samples": args.serve_saturated,
+                                   "samples_per_s": args.serve_saturated / dt,
+                                   "truncated_steps": int(sum(o[1]["truncated"] for o in out)),
+                                   "slots": args.serve_slots}
+        rng = np.random.default_rng(2)
+        res["poisson"] = []
+        for mult in (0.5, 0.8, 1.0):
+            lam = mult * plain_rate
+            gaps = rng.exponential(1.0 / lam, args.serve_poisson)
+            t0 = time.perf_counter()
+            rids = []
+            for i, gap in enumerate(gaps):
+                target = t0 + gaps[: i + 1].sum()
+                now = time.perf_counter()
+                if target > now:
+                    time.sleep(target - now)
+                rids.append(smp.submit(5000 + 100 * int(mult * 10) + i))
+            outs = [smp.wait(rr, timeout=900) for rr in rids]
+            span = time.perf_counter() - t0
+            lats = np.array([o[1]["latency_s"] for o in outs])
+            res["poisson"].append({"rate_x_plain": mult, "arrival_per_s": lam,
+                                   "requests": len(outs), "samples_per_s": len(outs) / span,
+                                   "p50_s": float(np.median(lats)),
+                                   "p99_s": float(np.quantile(lats, 0.99))})
+    res["served_vs_plain_samples_per_s"] = res["served_saturated"]["samples_per_s"] / plain_rate
+    return res
+
+
 # ------------------------------------------------------------------ reference arm
 
 def run_reference(args, rank, world):
@@ -385,6 +445,11 @@ def main(argv=None):
     p.add_argument("--n", type=int, default=40)
     p.add_argument("--no-n50", dest="n50", action="store_false")
     p.add_argument("--no-batch", dest="batch", action="store_false")
+    p.add_argument("--no-serving", dest="serving", action="store_false")
+    p.add_argument("--serve-plain", type=int, default=6)
+    p.add_argument("--serve-saturated", type=int, default=192)
+    p.add_argument("--serve-slots", type=int, default=256)
+    p.add_argument("--serve-poisson", type=int, default=24)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--ref-step-seconds", type=float, default=4.0)
