@@ -105,6 +105,11 @@ int gbsh_lhaf_async(const gbsh_c128* dA, int N, int lda, gbsh_c128* d_out, doubl
  * batched GBS workload: max 5e-7 at N=2, 2.1e-6 at N=4, 2.3e-5 at N=6); FP64 otherwise. */
 #define GBSH_PREC_MIXED 2
 #define GBSH_C32_MAX_N 4
+/* GBSH_PREC_DD: each subset term in double-double arithmetic (~106-bit significand): about
+ * 25x the FP64 cost, for results whose FP64 rounding floor (unit roundoff times the
+ * cancellation of the signed subset sum) is too coarse; the cross-subset sum is the same
+ * compensated FP64 sum. */
+#define GBSH_PREC_DD 3
 
 /*
  * gbsh_lhaf_batch — loop hafnians of `count` matrices of uneven size in one persistent
@@ -115,7 +120,8 @@ int gbsh_lhaf_async(const gbsh_c128* dA, int N, int lda, gbsh_c128* d_out, doubl
  *   outs      host array of `count` gbsh_c128 (results in input order).
  *   abs_sums  host array of `count` doubles or NULL: sum_Z |Re p_Z| + |Im p_Z| per matrix.
  *   precision GBSH_PREC_FP64, GBSH_PREC_C32 (every matrix in FP32 per subset, at the
- *             caller's risk: use abs_sums to bound the error) or GBSH_PREC_MIXED.
+ *             caller's risk: use abs_sums to bound the error), GBSH_PREC_MIXED or
+ *             GBSH_PREC_DD.
  * Each matrix's subsets are split into chunks whose size depends only on its own N, so a
  * matrix's result is bit-identical alone (count = 1) and inside any batch. Problems are
  * ordered largest first (longest-processing-time order) for the persistent launch.

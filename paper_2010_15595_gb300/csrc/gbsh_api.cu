@@ -113,7 +113,7 @@ double err_from(double abs_sum, gbsh_c128 v) {
 
 
 // ---------------------------------------------------------------- batched evaluation
-int g_batch_warps[2][gbsh::kMaxN / 2 + 1] = {};  // per precision and n_max; 0 = default
+int g_batch_warps[4][gbsh::kMaxN / 2 + 1] = {};  // per precision and n_max; 0 = default
 using gbsh::BatchLayout;
 using gbsh::batch_layout;
 
@@ -131,7 +131,7 @@ int batch_run(BatchLayout& L, const std::vector<gbsh::BatchInput>& in, int count
 }
 
 bool valid_precision(int p) {
-  return p == GBSH_PREC_FP64 || p == GBSH_PREC_C32 || p == GBSH_PREC_MIXED;
+  return p == GBSH_PREC_FP64 || p == GBSH_PREC_C32 || p == GBSH_PREC_MIXED || p == GBSH_PREC_DD;
 }
 
 
@@ -502,7 +502,8 @@ int gbsh_gbs_prob_batch(const gbsh_c128* B, int M, int ldb, const gbsh_c128* gam
 }
 
 int gbsh_set_batch_tuning(int precision, int n_max, int warps_per_cta) {
-  if (precision != GBSH_PREC_FP64 && precision != GBSH_PREC_C32) return GBSH_EINVAL;
+  if (precision != GBSH_PREC_FP64 && precision != GBSH_PREC_C32 && precision != GBSH_PREC_DD)
+    return GBSH_EINVAL;
   if (n_max < 0 || n_max > gbsh::kMaxN / 2 || warps_per_cta < 0 || warps_per_cta > gbsh::kMaxWarps)
     return GBSH_EINVAL;
   std::lock_guard<std::mutex> lk(g_tune_mu);

@@ -115,13 +115,106 @@ __device__ __forceinline__ unsigned mag_key(float2 a) {
   return hx > hy ? hx : hy;
 }
 
-// Scalar-type traits: T is the per-subset complex type (double2 or float2).
+
+// ---- double-double (unevaluated sum hi + lo, ~106-bit significand) for the extended-
+// precision variant. Error-free transformations: TwoSum (Knuth), FMA-based TwoProduct;
+// addition and multiplication in the style of Dekker's double-length arithmetic with a
+// final renormalisation; reciprocal by one Newton step from the double reciprocal.
+struct dd {
+  double hi, lo;
+  dd() = default;
+  __device__ __forceinline__ explicit dd(double h) : hi(h), lo(0.0) {}
+  __device__ __forceinline__ dd(double h, double l) : hi(h), lo(l) {}
+};
+__device__ __forceinline__ dd dd_make(double a) { return dd{a, 0.0}; }
+__device__ __forceinline__ void two_sum_d(double a, double b, double& s, double& e) {
+  s = a + b;
+  const double bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void quick_two_sum_d(double a, double b, double& s, double& e) {
+  s = a + b;
+  e = b - (s - a);
+}
+__device__ __forceinline__ dd operator+(dd x, dd y) {
+  double s, e, t, f;
+  two_sum_d(x.hi, y.hi, s, e);
+  two_sum_d(x.lo, y.lo, t, f);
+  e += t;
+  quick_two_sum_d(s, e, s, e);
+  e += f;
+  quick_two_sum_d(s, e, s, e);
+  return dd{s, e};
+}
+__device__ __forceinline__ dd operator-(dd x) { return dd{-x.hi, -x.lo}; }
+__device__ __forceinline__ dd operator-(dd x, dd y) { return x + (-y); }
+__device__ __forceinline__ dd operator*(dd x, dd y) {
+  const double p = x.hi * y.hi;
+  double e = fma(x.hi, y.hi, -p);
+  e = fma(x.hi, y.lo, e);
+  e = fma(x.lo, y.hi, e);
+  double s, t;
+  quick_two_sum_d(p, e, s, t);
+  return dd{s, t};
+}
+// a*b + c in each real type of the per-subset arithmetic
+__device__ __forceinline__ double rfma(double a, double b, double c) { return ::fma(a, b, c); }
+__device__ __forceinline__ float rfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ dd rfma(dd a, dd b, dd c) { return a * b + c; }
+__device__ __forceinline__ dd dd_recip(dd x) {
+  const double r0 = 1.0 / x.hi;
+  const dd r = dd_make(r0);
+  const dd e = dd_make(1.0) - x * r;  // 1 - x r0
+  return r + r * e;
+}
+
+struct ddc {
+  dd x, y;
+};
+__device__ __forceinline__ ddc cadd(ddc a, ddc b) { return ddc{a.x + b.x, a.y + b.y}; }
+__device__ __forceinline__ ddc cmul(ddc a, ddc b) {
+  return ddc{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+__device__ __forceinline__ ddc cfma(ddc acc, ddc a, ddc b) {
+  return ddc{acc.x + (a.x * b.x - a.y * b.y), acc.y + (a.x * b.y + a.y * b.x)};
+}
+__device__ __forceinline__ ddc cfms(ddc acc, ddc a, ddc b) {
+  return ddc{acc.x - (a.x * b.x - a.y * b.y), acc.y - (a.x * b.y + a.y * b.x)};
+}
+__device__ __forceinline__ ddc cscale(ddc a, dd s) { return ddc{a.x * s, a.y * s}; }
+__device__ __forceinline__ ddc crecip(ddc a) {
+  const dd r = dd_recip(a.x * a.x + a.y * a.y);
+  return ddc{a.x * r, -(a.y * r)};
+}
+__device__ __forceinline__ dd shfl_d(dd v, int src) {
+  return dd{__shfl_sync(FULL, v.hi, src), __shfl_sync(FULL, v.lo, src)};
+}
+__device__ __forceinline__ ddc shfl_c(ddc v, int src) { return ddc{shfl_d(v.x, src), shfl_d(v.y, src)}; }
+__device__ __forceinline__ ddc shfl_up_c(ddc v, unsigned d) {
+  return ddc{dd{__shfl_up_sync(FULL, v.x.hi, d), __shfl_up_sync(FULL, v.x.lo, d)},
+             dd{__shfl_up_sync(FULL, v.y.hi, d), __shfl_up_sync(FULL, v.y.lo, d)}};
+}
+__device__ __forceinline__ ddc shfl_down_c(ddc v, unsigned d) {
+  return ddc{dd{__shfl_down_sync(FULL, v.x.hi, d), __shfl_down_sync(FULL, v.x.lo, d)},
+             dd{__shfl_down_sync(FULL, v.y.hi, d), __shfl_down_sync(FULL, v.y.lo, d)}};
+}
+__device__ __forceinline__ unsigned mag_key(ddc a) { return mag_key(make_double2(a.x.hi, a.y.hi)); }
+
+// Scalar-type traits: T is the per-subset complex type (double2, float2 or ddc).
 template <class T> struct Cx;
 template <> struct Cx<double2> {
   using R = double;
   __device__ __forceinline__ static double2 make(double a, double b) { return make_double2(a, b); }
   __device__ __forceinline__ static double2 from(double2 v) { return v; }
   __device__ __forceinline__ static double2 to_d(double2 v) { return v; }
+};
+template <> struct Cx<ddc> {
+  using R = dd;
+  __device__ __forceinline__ static ddc make(dd a, dd b) { return ddc{a, b}; }
+  __device__ __forceinline__ static ddc from(double2 v) { return ddc{dd_make(v.x), dd_make(v.y)}; }
+  __device__ __forceinline__ static double2 to_d(ddc v) {
+    return make_double2(v.x.hi + v.x.lo, v.y.hi + v.y.lo);
+  }
 };
 template <> struct Cx<float2> {
   using R = float;
@@ -135,6 +228,12 @@ template <> struct Cx<float2> {
 // 1/k for k = 0..63 (entry 0 unused), filled by the host with correctly rounded values.
 // Defined here because this header is included by exactly one translation unit.
 __constant__ double c_inv_int[64];
+
+// 1/k in the real type R of the per-subset arithmetic (exact to that type's precision).
+template <class R> __device__ __forceinline__ R inv_int(int k);
+template <> __device__ __forceinline__ double inv_int<double>(int k) { return c_inv_int[k]; }
+template <> __device__ __forceinline__ float inv_int<float>(int k) { return (float)c_inv_int[k]; }
+template <> __device__ __forceinline__ dd inv_int<dd>(int k) { return dd_recip(dd((double)k)); }
 
 // Compensated (two-sum) accumulator for the signed subset sum.
 struct DDAcc {
@@ -338,7 +437,7 @@ __device__ __noinline__ double2 subset_term(const Problem& P, uint64_t z, int k,
     if (lane > s) tr = cfms(tr, qs, ts);
   }
   // (c) j c_j = (t_j + j l_j) / 2
-  const T icj = Cx<T>::make(R(0.5) * fma((R)lane, lj.x, tr.x), R(0.5) * fma((R)lane, lj.y, tr.y));
+  const T icj = Cx<T>::make(R(0.5) * rfma((R)lane, lj.x, tr.x), R(0.5) * rfma((R)lane, lj.y, tr.y));
   // (d) exp-polynomial: j p_j = sum_{i=1}^{j} i c_i p_{j-i}, p_0 = 1
   T acc = zero;
   for (int s = 0; s < n; ++s) {
@@ -346,12 +445,12 @@ __device__ __noinline__ double2 subset_term(const Problem& P, uint64_t z, int k,
     if (s == 0) {
       ps = Cx<T>::make(R(1), R(0));
     } else {
-      ps = cscale(shfl_c(acc, s), (R)c_inv_int[s]);
+      ps = cscale(shfl_c(acc, s), inv_int<R>(s));
     }
     T ics = shfl_up_c(icj, s);
     if (lane > s) acc = cfma(acc, ics, ps);
   }
-  T pn = cscale(shfl_c(acc, n), (R)c_inv_int[n]);
+  T pn = cscale(shfl_c(acc, n), inv_int<R>(n));
   __syncwarp();
   return Cx<T>::to_d(pn);
 }

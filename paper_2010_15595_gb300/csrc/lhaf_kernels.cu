@@ -282,6 +282,9 @@ cudaError_t device_info(DeviceInfo* info) {
     e = cudaFuncSetAttribute(lhaf_batch_kernel<float2>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, d.smem_optin);
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(lhaf_batch_kernel<ddc>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, d.smem_optin);
+    if (e != cudaSuccess) return e;
     g_info[dev] = d;
     g_info_done[dev] = true;
   }
@@ -459,7 +462,7 @@ cudaError_t launch_visit_count(const LhafPlan& plan, unsigned* counts, void* ws,
 namespace gbsh {
 
 int batch_warps_for(int n_max, int precision, const DeviceInfo& dev, int warps_pref) {
-  const int esz = precision == kPrecC32 ? (int)sizeof(float2) : (int)sizeof(double2);
+  const int esz = prec_elem_bytes(precision);
   const size_t area = (size_t)warp_area_elems(n_max, n_max, esz) * esz;
   int W = warps_pref > 0 ? warps_pref : 8;
   if (W > kMaxWarps) W = kMaxWarps;
@@ -482,13 +485,15 @@ cudaError_t launch_batch(const BatchInput* d_in, const BatchProblem* d_prob, int
   e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned), stream);
   if (e != cudaSuccess) return e;
   if (total_chunks > 0) {
-    const bool c32 = precision == kPrecC32;
-    const int esz = c32 ? (int)sizeof(float2) : (int)sizeof(double2);
+    const int esz = prec_elem_bytes(precision);
     const int area = warp_area_elems(n_max > 0 ? n_max : 1, n_max > 0 ? n_max : 1, esz);
-    const size_t smem = (size_t)warps * area * (c32 ? sizeof(float2) : sizeof(double2));
+    const size_t smem = (size_t)warps * area * esz;
     int per_sm = 1;
-    if (c32) {
+    if (precision == kPrecC32) {
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lhaf_batch_kernel<float2>,
+                                                    32 * warps, smem);
+    } else if (precision == kPrecDD) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lhaf_batch_kernel<ddc>,
                                                     32 * warps, smem);
     } else {
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lhaf_batch_kernel<double2>,
@@ -498,8 +503,11 @@ cudaError_t launch_batch(const BatchInput* d_in, const BatchProblem* d_prob, int
     unsigned blocks = (unsigned)(per_sm * dev.sm_count);
     const unsigned need = (total_chunks + warps - 1) / warps;
     if (blocks > need) blocks = need;
-    if (c32) {
+    if (precision == kPrecC32) {
       lhaf_batch_kernel<float2><<<blocks, 32 * warps, smem, stream>>>(
+          d_prob, count, total_chunks, area, d_counter, d_partials);
+    } else if (precision == kPrecDD) {
+      lhaf_batch_kernel<ddc><<<blocks, 32 * warps, smem, stream>>>(
           d_prob, count, total_chunks, area, d_counter, d_partials);
     } else {
       lhaf_batch_kernel<double2><<<blocks, 32 * warps, smem, stream>>>(

@@ -40,6 +40,12 @@ struct BatchInput {
 // the cross-subset sum still compensated in FP64.
 constexpr int kPrecFP64 = 0;
 constexpr int kPrecC32 = 1;
+constexpr int kPrecDD = 3;  // double-double per subset (value 2 is the API's mixed mode)
+
+// Bytes of one complex element of the per-subset arithmetic of a precision.
+__host__ __device__ inline int prec_elem_bytes(int precision) {
+  return precision == kPrecC32 ? 8 : (precision == kPrecDD ? 32 : 16);
+}
 
 // Chunk size of a batched problem with n pairs: a function of n alone.
 __host__ __device__ inline unsigned long long batch_chunk_size(int n) {

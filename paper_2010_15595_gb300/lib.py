@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libgbsh.so")
 
 GBSH_OK, GBSH_EINVAL, GBSH_ENOMEM, GBSH_ECUDA, GBSH_ETIMEOUT, GBSH_PENDING, GBSH_ENOTFOUND = range(7)
 MAX_N = 60
-PREC_FP64, PREC_C32, PREC_MIXED = 0, 1, 2
+PREC_FP64, PREC_C32, PREC_MIXED, PREC_DD = 0, 1, 2, 3
 # Largest N for which the complex-FP32 per-subset variant is enabled (GBSH_C32_MAX_N): its
 # measured error against the FP64 path stays <= 1e-5 relative up to this size.
 C32_MAX_N = 4

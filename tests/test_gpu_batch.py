@@ -116,3 +116,30 @@ def test_batch_rejects_bad_input(gbsh):
         gbsh.lhaf_batch([np.ones((61, 61), complex)])
     with pytest.raises(gbsh.GbshError):
         gbsh.gbs_prob_batch(np.eye(3, dtype=complex), np.zeros(3, complex), np.array([[1, -1, 0]]))
+
+
+def test_double_double_meets_stated_tolerance(gbsh):
+    """Double-double per-subset arithmetic (GBSH_PREC_DD) removes the FP64 rounding floor:
+    within 1e-9 of the long-double oracle where FP64 cannot get there (N=32..40)."""
+    from paper_2010_15595_gb300.lib import PREC_DD
+    from tests.test_gpu_parity import _golden
+    A40, rec = _golden("lhaf_n40")
+    mats = [W.single_lhaf_mid(32), A40]
+    refs = [L.lhaf_subset_ld(mats[0]), complex(*rec["lhaf_ld"])]
+    got = gbsh.lhaf_batch(mats, precision=PREC_DD)
+    for g, ref in zip(got, refs):
+        assert abs(g - ref) <= 1e-9 * abs(ref), (g, ref, abs(g - ref) / abs(ref))
+
+
+def test_double_double_small_vs_definition(gbsh):
+    """Against the long-double oracle; the gate is that oracle's own rounding floor
+    (64-bit significand, same random-walk model as the FP64 gate), not the GPU's."""
+    from paper_2010_15595_gb300.lib import PREC_DD
+    rng = np.random.default_rng(21)
+    mats = [W.random_complex_symmetric(N, rng) for N in (1, 2, 5, 9, 14, 20)]
+    got = gbsh.lhaf_batch(mats, precision=PREC_DD)
+    for A, g in zip(mats, got):
+        ref = L.lhaf_subset_ld(A)
+        _, _, sq = L.lhaf_subset_stats(A)
+        tol = max(1e-14, 512 * 2.0 ** -64 * sq ** 0.5 / abs(ref))
+        assert abs(g - ref) <= tol * abs(ref), (A.shape, g, ref)
