@@ -403,6 +403,46 @@ def run_serving_workload(args):
     return res
 
 
+def fig1_tvd(modes=(1, 2, 3, 4, 5, 6), unitaries=10, samples=200000, r=0.5, cutoff=6, seed0=0):
+    """Sec. III, Fig. 1: percent TVD between exact output probabilities and (a) the served
+    chain-rule sampler, (b) exact sampling of the same size, for m modes with squeezing r in
+    every mode and Fock cutoff `cutoff`, averaged over Haar-random unitaries. The TVD runs
+    over the outputs with at most `cutoff` photons in total. Exact probabilities come from
+    the GPU loop hafnians (gbsh_gbs_prob_batch)."""
+    import itertools
+    import numpy as np
+    from paper_2010_15595_gb300 import lib, sampler as S, workloads
+    rows = []
+    for m in modes:
+        pats = [p for p in itertools.product(range(cutoff + 1), repeat=m) if sum(p) <= cutoff]
+        index = {p: i for i, p in enumerate(pats)}
+        alg, exp_ = [], []
+        for u in range(unitaries):
+            rng = workloads.rng_for(70 + m, seed0 + u)
+            U = workloads.haar_unitary(m, rng)
+            st = S.pure_state(U, np.full(m, r), np.zeros(m, complex))
+            probs, _ = lib.gbs_prob_batch(st.B, st.gamma, np.array(pats, dtype=np.int32),
+                                          p_vacs=np.full(len(pats), st.p_vac))
+            rest = max(0.0, 1.0 - probs.sum())
+            per_req = 4000
+            with S.Sampler(st, cutoff=cutoff, n_cap=60, max_active=4096) as smp:
+                rids = [smp.submit(1_000_000 * m + 1000 * u + q, per_req)
+                        for q in range((samples + per_req - 1) // per_req)]
+                out = np.concatenate([smp.wait(rr, timeout=1800)[0] for rr in rids])[:samples]
+            counts = np.zeros(len(pats))
+            for row in out:
+                key = tuple(int(x) for x in row)
+                if key in index:
+                    counts[index[key]] += 1
+            alg.append(50.0 * np.abs(counts / samples - probs).sum())
+            rs = np.random.default_rng(seed0 + u)
+            draw = rs.multinomial(samples, np.append(probs, rest) / (probs.sum() + rest))[:-1]
+            exp_.append(50.0 * np.abs(draw / samples - probs).sum())
+        rows.append({"modes": m, "algorithm_tvd_pct": [float(np.mean(alg)), float(np.std(alg))],
+                     "expected_tvd_pct": [float(np.mean(exp_)), float(np.std(exp_))]})
+    return rows
+
+
 # ------------------------------------------------------------------ reference arm
 
 def run_reference(args, rank, world):
@@ -450,12 +490,21 @@ def main(argv=None):
     p.add_argument("--serve-saturated", type=int, default=192)
     p.add_argument("--serve-slots", type=int, default=256)
     p.add_argument("--serve-poisson", type=int, default=24)
+    p.add_argument("--fig1", action="store_true",
+                   help="run the Fig. 1 TVD experiment (Sec. III) instead of the benchmark")
+    p.add_argument("--fig1-samples", type=int, default=200000)
+    p.add_argument("--fig1-unitaries", type=int, default=10)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--ref-step-seconds", type=float, default=4.0)
     args = p.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
+    if args.fig1:
+        rows = fig1_tvd(samples=args.fig1_samples, unitaries=args.fig1_unitaries)
+        print(json.dumps({"experiment": "Fig. 1 TVD", "samples": args.fig1_samples,
+                          "unitaries": args.fig1_unitaries, "rows": rows}), flush=True)
+        return
     rank, world, local_rank = dist_env()
     if world > 1:
         import torch

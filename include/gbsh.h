@@ -239,6 +239,8 @@ typedef struct {
                                0: plain path, one launch per loop hafnian, one sample at a time */
   int precision;            /* GBSH_PREC_FP64 or GBSH_PREC_C32 */
   int device;               /* CUDA device the sampler's worker thread uses */
+  int threshold;            /* 1: report threshold-detector clicks (s_i > 0 -> 1), the
+                               post-processing of the end of Sec. III; 0: photon numbers */
 } gbsh_sampler_cfg;
 
 typedef struct {

@@ -180,7 +180,7 @@ struct gbsh_sampler {
   int tick(std::vector<Chain>& active);
   int ensure_ws(size_t bytes);
   int ensure_idx(size_t n);
-  size_t chain_mem_estimate() const;
+  size_t chain_mem_estimate(int nphot) const;
 };
 
 namespace {
@@ -191,13 +191,17 @@ int from_cuda(cudaError_t e) {
 
 }  // namespace
 
-size_t gbsh_sampler::chain_mem_estimate() const {
-  // device bytes of one chain's candidates at the largest allowed size
-  const int N = cfg.n_cap;
-  const int Ne = N + (N & 1), n = Ne / 2;
-  const size_t chunks = ((size_t)1 << n) / gbsh::batch_chunk_size(n);
-  const size_t per = sizeof(double2) * ((size_t)Ne * Ne + Ne) + 40 * chunks + 128 + 4 * (size_t)N;
-  return per * (size_t)(cfg.cutoff + 1);
+size_t gbsh_sampler::chain_mem_estimate(int nphot) const {
+  // device bytes of the next tick's candidates of a chain with nphot photons so far
+  size_t total = 0;
+  for (int s = 0; s <= cfg.cutoff; ++s) {
+    const int N = nphot + s;
+    if (N > cfg.n_cap) break;
+    const int Ne = N + (N & 1), n = Ne / 2;
+    const size_t chunks = n > 0 ? ((size_t)1 << n) / gbsh::batch_chunk_size(n) : 0;
+    total += sizeof(double2) * ((size_t)Ne * Ne + Ne) + 40 * chunks + 128 + 4 * (size_t)N;
+  }
+  return total;
 }
 
 int gbsh_sampler::ensure_ws(size_t bytes) {
@@ -334,15 +338,19 @@ int gbsh_sampler::tick(std::vector<Chain>& active) {
 void gbsh_sampler::run() {
   int rc = from_cuda(cudaSetDevice(device));
   std::vector<Chain> active;
-  size_t mem_in_use = 0;
-  const size_t per_chain = chain_mem_estimate();
+  size_t mem_in_use = 0;  // estimate for the next tick of the admitted chains
   const int max_active = cfg.batching ? std::max(1, cfg.max_active) : 1;
+  const int R = 2 * (cfg.M - 1);
+  std::vector<double> z(R), quad(R);
+  std::vector<double2> alpha_stage;
   while (rc == GBSH_OK) {
     {
       std::unique_lock<std::mutex> lk(mu);
-      // admission: by free slots and by device-memory budget
-      while (!pending.empty() && (int)active.size() < max_active &&
-             (active.empty() || mem_in_use + per_chain <= cfg.mem_budget)) {
+      // admission: by free slots and by the device-memory budget of the next tick
+      size_t first_new = active.size();
+      while (!pending.empty() && (int)active.size() < max_active) {
+        const size_t need = chain_mem_estimate(0);
+        if (!active.empty() && mem_in_use + need > cfg.mem_budget) break;
         Chain ch = std::move(pending.front());
         pending.pop_front();
         if (ch.req->cancelled) continue;
@@ -352,45 +360,46 @@ void gbsh_sampler::run() {
         }
         ch.slot = free_slots.back();
         free_slots.pop_back();
-        ch.mem = per_chain;
-        mem_in_use += per_chain;
+        ch.mem = need;
+        mem_in_use += need;
         active.push_back(std::move(ch));
-        Chain& a = active.back();
-        // step 2: heterodyne outcomes of modes 2..M from the Husimi distribution
-        const int R = 2 * (cfg.M - 1);
-        std::vector<double> z(R), mu(R);
+      }
+      if (active.empty()) {
+        if (stop) break;
+        cv_work.wait_for(lk, std::chrono::milliseconds(20));
+        continue;
+      }
+      lk.unlock();
+      // step 2 for the newly admitted chains: heterodyne outcomes of modes 2..M from the
+      // Husimi distribution, staged and copied to their device slots
+      for (size_t c = first_new; c < active.size(); ++c) {
+        Chain& a = active[c];
         chain_normals(a.req->seed, a.chain_no, R, z.data());
         for (int r = 0; r < R; ++r) {
           double acc = het_mean[r];
-          for (int c = 0; c <= r; ++c) acc += het_chol[(size_t)r * R + c] * z[c];
-          mu[r] = acc;
+          for (int q = 0; q <= r; ++q) acc += het_chol[(size_t)r * R + q] * z[q];
+          quad[r] = acc;
         }
-        std::vector<double2> alpha(cfg.M, make_double2(0.0, 0.0));
+        alpha_stage.assign(cfg.M, make_double2(0.0, 0.0));
         for (int j = 1; j < cfg.M; ++j)  // alpha = (q + i p) / 2   (hbar = 2)
-          alpha[j] = make_double2(0.5 * mu[j - 1], 0.5 * mu[(cfg.M - 1) + j - 1]);
-        lk.unlock();
-        cudaError_t e = cudaMemcpyAsync(dalpha + (size_t)a.slot * cfg.M, alpha.data(),
+          alpha_stage[j] = make_double2(0.5 * quad[j - 1], 0.5 * quad[(cfg.M - 1) + j - 1]);
+        cudaError_t e = cudaMemcpyAsync(dalpha + (size_t)a.slot * cfg.M, alpha_stage.data(),
                                         sizeof(double2) * cfg.M, cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        lk.lock();
         if (e != cudaSuccess) {
           rc = from_cuda(e);
           break;
         }
       }
       if (rc != GBSH_OK) break;
-      if (active.empty()) {
-        if (stop) break;
-        cv_work.wait_for(lk, std::chrono::milliseconds(20));
-        continue;
-      }
     }
     rc = tick(active);
     if (rc != GBSH_OK) break;
-    // retire finished chains
+    // retire finished chains, refresh the memory estimate of the others
     std::lock_guard<std::mutex> lk(mu);
     std::vector<Chain> keep;
+    keep.reserve(active.size());
     std::map<Request*, bool> ticked;
+    mem_in_use = 0;
     for (auto& ch : active) {
       if (!ticked[ch.req.get()]) {
         ch.req->ticks += 1;
@@ -398,8 +407,9 @@ void gbsh_sampler::run() {
       }
       if (ch.k >= cfg.M || ch.req->cancelled) {
         if (!ch.req->cancelled) {
-          std::memcpy(&ch.req->samples[(size_t)ch.chain_no * cfg.M], ch.s.data(),
-                      sizeof(int) * cfg.M);
+          int* out = &ch.req->samples[(size_t)ch.chain_no * cfg.M];
+          for (int i = 0; i < cfg.M; ++i)  // threshold detectors: click iff s_i > 0
+            out[i] = cfg.threshold ? (ch.s[i] > 0 ? 1 : 0) : ch.s[i];
           ch.req->done += 1;
           if (ch.req->done == ch.req->n_samples) {
             ch.req->finished = true;
@@ -408,8 +418,9 @@ void gbsh_sampler::run() {
           }
         }
         free_slots.push_back(ch.slot);
-        mem_in_use -= ch.mem;
       } else {
+        ch.mem = chain_mem_estimate(ch.nphot);
+        mem_in_use += ch.mem;
         keep.push_back(std::move(ch));
       }
     }

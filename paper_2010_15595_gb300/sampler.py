@@ -78,7 +78,8 @@ class _Cfg(ctypes.Structure):
                 ("gamma", ctypes.c_void_p), ("het_mean", ctypes.c_void_p),
                 ("het_chol", ctypes.c_void_p), ("cutoff", ctypes.c_int), ("n_cap", ctypes.c_int),
                 ("max_active", ctypes.c_int), ("mem_budget", ctypes.c_size_t),
-                ("batching", ctypes.c_int), ("precision", ctypes.c_int), ("device", ctypes.c_int)]
+                ("batching", ctypes.c_int), ("precision", ctypes.c_int), ("device", ctypes.c_int),
+                ("threshold", ctypes.c_int)]
 
 
 class ReqStats(ctypes.Structure):
@@ -125,7 +126,7 @@ class Sampler:
 
     def __init__(self, state: PureState, cutoff: int = 4, n_cap: int = 36, max_active: int = 256,
                  mem_budget: int = 2 << 30, batching: bool = True,
-                 precision: int = _lib.PREC_FP64, device: int = 0):
+                 precision: int = _lib.PREC_FP64, device: int = 0, threshold: bool = False):
         self.so = _bind()
         self.M = state.B.shape[0]
         self._B = np.ascontiguousarray(state.B, dtype=np.complex128)
@@ -136,7 +137,7 @@ class Sampler:
                    self._m.ctypes.data if self._m.size else None,
                    self._L.ctypes.data if self._L.size else None, cutoff, n_cap,
                    max_active if batching else 1, mem_budget, 1 if batching else 0, precision,
-                   device)
+                   device, 1 if threshold else 0)
         h = ctypes.c_void_p()
         _lib._check(self.so.gbsh_sampler_create(ctypes.byref(cfg), ctypes.byref(h)),
                     "gbsh_sampler_create")

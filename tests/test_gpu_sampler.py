@@ -100,3 +100,35 @@ def test_bounded_wait_and_cancel():
         assert e.value.code == lib.GBSH_ETIMEOUT
         smp.cancel(rids[-1])
         assert smp.poll(rids[0]) is None or True
+
+
+def test_threshold_detectors_are_clicks_of_photon_samples():
+    """End of Sec. III: threshold detectors report s_i = 1 if s_i > 0 (same seeds)."""
+    from paper_2010_15595_gb300 import sampler as S
+    U, rv, al = _phys(5, 7, r=0.7)
+    st = S.pure_state(U, rv, al)
+    with S.Sampler(st, cutoff=4, n_cap=40, max_active=32) as a:
+        photons = _run(a, range(6), n_samples=2)
+    with S.Sampler(st, cutoff=4, n_cap=40, max_active=32, threshold=True) as b:
+        clicks = _run(b, range(6), n_samples=2)
+    for p, c in zip(photons, clicks):
+        assert np.array_equal(c, np.minimum(p, 1))
+
+
+def test_fig1_tvd_reduced():
+    """Fig. 1 in small (1-3 modes, r = 0.5, cutoff 6, 20000 samples, 3 unitaries): the
+    sampler's TVD to the exact distribution matches the TVD of exact sampling; and the
+    expected TVD scales like the paper's printed values (200000 samples) times
+    sqrt(200000/20000) within a factor 2."""
+    import bench
+    import os
+    rows = bench.fig1_tvd(modes=(1, 2, 3), unitaries=3, samples=20000)
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "fig1_tvd.txt")
+    paper = {int(r[0]): [float(x) for x in r[1:]] for r in
+             (line.split() for line in open(here) if line.strip() and not line.startswith("#"))}
+    for row in rows:
+        a_mean, a_std = row["algorithm_tvd_pct"]
+        e_mean, e_std = row["expected_tvd_pct"]
+        assert abs(a_mean - e_mean) <= 3 * (a_std + e_std) + 0.05 * e_mean, row
+        scaled = paper[row["modes"]][0] * (200000 / 20000) ** 0.5
+        assert 0.5 * scaled <= e_mean <= 2.0 * scaled, (row, scaled)
