@@ -132,3 +132,28 @@ def test_fig1_tvd_reduced():
         assert abs(a_mean - e_mean) <= 3 * (a_std + e_std) + 0.05 * e_mean, row
         scaled = paper[row["modes"]][0] * (200000 / 20000) ** 0.5
         assert 0.5 * scaled <= e_mean <= 2.0 * scaled, (row, scaled)
+
+
+def test_chi_square_goodness_of_fit():
+    """200000 samples of a 3-mode state (r = 0.5, cutoff 6) against exact probabilities
+    from the oracle: chi-square over bins with >= 5 expected counts is not significant."""
+    import itertools
+    from scipy import stats
+    from paper_2010_15595_gb300 import sampler as S
+    m, n = 3, 200000
+    U, rv, _ = _phys(m, 11)
+    al = W.complex_normal(m, 0.2, W.rng_for(61, 0))
+    st = S.pure_state(U, rv, al)
+    V, R = G.pure_state_covariance(U, rv), G.means_from_alpha(al)
+    B, g, pv = G.pure_B_gamma(V, R)
+    pats = [p for p in itertools.product(range(7), repeat=m) if sum(p) <= 9]
+    probs = np.array([G.prob_pure(B, g, pv, list(p)) for p in pats])
+    with S.Sampler(st, cutoff=6, n_cap=60, max_active=4096) as smp:
+        out = np.concatenate(_run(smp, list(range(500, 520)), n_samples=n // 20))
+    base = 7 ** np.arange(m)
+    cnt = np.bincount((np.minimum(out, 6) * base).sum(1), minlength=7 ** m)
+    O = np.array([cnt[(np.array(p) * base).sum()] for p in pats], float)
+    E = probs * n
+    sel = E >= 5
+    chi2 = ((O[sel] - E[sel]) ** 2 / E[sel]).sum()
+    assert stats.chi2.sf(chi2, sel.sum() - 1) > 1e-3, chi2
