@@ -444,6 +444,42 @@ def fig1_tvd(modes=(1, 2, 3, 4, 5, 6), unitaries=10, samples=200000, r=0.5, cuto
     return rows
 
 
+def telephone(n: int) -> int:
+    """T(n) = lhaf(all-ones n x n) (number of matchings with loops; Fig. 2 caption)."""
+    a, b_ = 1, 1
+    for k in range(2, n + 1):
+        a, b_ = b_, b_ + (k - 1) * a
+    return b_ if n >= 1 else 1
+
+
+def fig2_allones(sizes_fp64=range(30, 58, 2), sizes_dd=range(30, 48, 2)):
+    """Sec. IV, Fig. 2: relative error of lhaf(all-ones n x n) against T(n), with the FP64
+    kernels (gbsh_lhaf) and the double-double per-subset variant (batched entry point)."""
+    from fractions import Fraction
+    import numpy as np
+    from paper_2010_15595_gb300 import lib
+
+    def rel(v, n):
+        T = telephone(n)
+        return float(abs(Fraction(v.real) - T) / T), abs(v.imag) / T
+
+    rows = []
+    for n in sizes_fp64:
+        A = np.ones((n, n), dtype=np.complex128)
+        t = time.perf_counter()
+        v = lib.lhaf(A)
+        dt = time.perf_counter() - t
+        row = {"n": n, "fp64_rel_err": rel(v, n)[0], "fp64_seconds": dt}
+        if n in sizes_dd:
+            t = time.perf_counter()
+            vd = lib.lhaf_batch([A], precision=lib.PREC_DD)[0]
+            row["dd_rel_err"] = rel(vd, n)[0]
+            row["dd_seconds"] = time.perf_counter() - t
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+    return rows
+
+
 # ------------------------------------------------------------------ reference arm
 
 def run_reference(args, rank, world):
@@ -494,6 +530,8 @@ def main(argv=None):
     p.add_argument("--fig1", action="store_true",
                    help="run the Fig. 1 TVD experiment (Sec. III) instead of the benchmark")
     p.add_argument("--fig1-samples", type=int, default=200000)
+    p.add_argument("--fig2", action="store_true",
+                   help="run the Fig. 2 all-ones accuracy study (Sec. IV) instead of the benchmark")
     p.add_argument("--fig1-unitaries", type=int, default=10)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -501,6 +539,10 @@ def main(argv=None):
     args = p.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
+    if args.fig2:
+        rows = fig2_allones()
+        print(json.dumps({"experiment": "Fig. 2 all-ones accuracy", "rows": rows}), flush=True)
+        return
     if args.fig1:
         rows = fig1_tvd(samples=args.fig1_samples, unitaries=args.fig1_unitaries)
         print(json.dumps({"experiment": "Fig. 1 TVD", "samples": args.fig1_samples,

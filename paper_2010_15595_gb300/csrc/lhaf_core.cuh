@@ -200,6 +200,12 @@ __device__ __forceinline__ ddc shfl_down_c(ddc v, unsigned d) {
 }
 __device__ __forceinline__ unsigned mag_key(ddc a) { return mag_key(make_double2(a.x.hi, a.y.hi)); }
 
+// A subset term handed to the accumulator: value hi + lo per component (lo = 0 unless the
+// per-subset arithmetic is double-double, whose low parts must not be rounded away).
+struct Term {
+  double re_hi, re_lo, im_hi, im_lo;
+};
+
 // Scalar-type traits: T is the per-subset complex type (double2, float2 or ddc).
 template <class T> struct Cx;
 template <> struct Cx<double2> {
@@ -207,6 +213,7 @@ template <> struct Cx<double2> {
   __device__ __forceinline__ static double2 make(double a, double b) { return make_double2(a, b); }
   __device__ __forceinline__ static double2 from(double2 v) { return v; }
   __device__ __forceinline__ static double2 to_d(double2 v) { return v; }
+  __device__ __forceinline__ static Term to_term(double2 v) { return Term{v.x, 0.0, v.y, 0.0}; }
 };
 template <> struct Cx<ddc> {
   using R = dd;
@@ -215,6 +222,7 @@ template <> struct Cx<ddc> {
   __device__ __forceinline__ static double2 to_d(ddc v) {
     return make_double2(v.x.hi + v.x.lo, v.y.hi + v.y.lo);
   }
+  __device__ __forceinline__ static Term to_term(ddc v) { return Term{v.x.hi, v.x.lo, v.y.hi, v.y.lo}; }
 };
 template <> struct Cx<float2> {
   using R = float;
@@ -223,6 +231,7 @@ template <> struct Cx<float2> {
     return make_float2((float)v.x, (float)v.y);
   }
   __device__ __forceinline__ static double2 to_d(float2 v) { return make_double2(v.x, v.y); }
+  __device__ __forceinline__ static Term to_term(float2 v) { return Term{v.x, 0.0, v.y, 0.0}; }
 };
 
 // 1/k for k = 0..63 (entry 0 unused), filled by the host with correctly rounded values.
@@ -250,6 +259,12 @@ struct DDAcc {
     two_sum(im_hi, x.y, s, e); im_hi = s; im_lo += e;
     abs_sum += fabs(x.x) + fabs(x.y);
   }
+  __device__ __forceinline__ void add(const Term& t) {
+    double s, e;
+    two_sum(re_hi, t.re_hi, s, e); re_hi = s; re_lo += e + t.re_lo;
+    two_sum(im_hi, t.im_hi, s, e); im_hi = s; im_lo += e + t.im_lo;
+    abs_sum += fabs(t.re_hi) + fabs(t.im_hi);
+  }
 };
 
 // ------------------------------------------------------------------------------------
@@ -260,8 +275,8 @@ struct DDAcc {
 // All 32 lanes must call it; every lane returns the same value.
 // ------------------------------------------------------------------------------------
 template <class T>
-__device__ __noinline__ double2 subset_term(const Problem& P, uint64_t z, int k,
-                                            T* __restrict__ area, int lane) {
+__device__ __noinline__ Term subset_term_full(const Problem& P, uint64_t z, int k,
+                                              T* __restrict__ area, int lane) {
   using R = typename Cx<T>::R;
   const int n = P.n;
   const int m = 2 * k;
@@ -452,7 +467,15 @@ __device__ __noinline__ double2 subset_term(const Problem& P, uint64_t z, int k,
   }
   T pn = cscale(shfl_c(acc, n), inv_int<R>(n));
   __syncwarp();
-  return Cx<T>::to_d(pn);
+  return Cx<T>::to_term(pn);
+}
+
+// p_Z rounded to complex double.
+template <class T>
+__device__ __forceinline__ double2 subset_term(const Problem& P, uint64_t z, int k,
+                                               T* __restrict__ area, int lane) {
+  const Term t = subset_term_full<T>(P, z, k, area, lane);
+  return make_double2(t.re_hi + t.re_lo, t.im_hi + t.im_lo);
 }
 
 }  // namespace gbsh

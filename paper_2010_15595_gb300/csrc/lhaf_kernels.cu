@@ -212,9 +212,9 @@ lhaf_batch_kernel(const BatchProblem* __restrict__ prob, int count, unsigned tot
       const uint64_t z = i ^ (i >> 1);
       const int k = __popcll(z);
       if (k == 0) continue;
-      double2 pz = subset_term<T>(P, z, k, area, lane);
-      if ((P.n - k) & 1) pz = make_double2(-pz.x, -pz.y);
-      acc.add(pz);
+      Term t = subset_term_full<T>(P, z, k, area, lane);
+      if ((P.n - k) & 1) t = Term{-t.re_hi, -t.re_lo, -t.im_hi, -t.im_lo};
+      acc.add(t);
     }
     if (lane == 0) {
       double* o = partials + (size_t)g * 5;

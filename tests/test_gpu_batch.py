@@ -143,3 +143,16 @@ def test_double_double_small_vs_definition(gbsh):
         _, _, sq = L.lhaf_subset_stats(A)
         tol = max(1e-14, 512 * 2.0 ** -64 * sq ** 0.5 / abs(ref))
         assert abs(g - ref) <= tol * abs(ref), (A.shape, g, ref)
+
+
+def test_double_double_all_ones_telephone(gbsh):
+    """Fig. 2's accuracy pin: lhaf(all-ones) = T(n). In double-double (terms accumulated
+    without rounding their low parts) the error stays at the final rounding, far below the
+    paper's long-double values (3.6e-12 at n=30, 3.4e-10 at n=36)."""
+    from paper_2010_15595_gb300.lib import PREC_DD
+    from fractions import Fraction
+    import bench
+    for n in (30, 36):
+        v = gbsh.lhaf_batch([W.all_ones(n)], precision=PREC_DD)[0]
+        T = bench.telephone(n)
+        assert float(abs(Fraction(v.real) - T) / T) <= 1e-13, (n, v, T)
