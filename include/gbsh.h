@@ -241,6 +241,15 @@ typedef struct {
   int device;               /* CUDA device the sampler's worker thread uses */
   int threshold;            /* 1: report threshold-detector clicks (s_i > 0 -> 1), the
                                post-processing of the end of Sec. III; 0: photon numbers */
+  /* Mixed states (step 1 of Sec. III, Eqs. split/decomp/mnpdf): with mixed = 1, B and
+   * het_chol describe the pure part T of the Williamson split V = T + W, and every sample
+   * first draws its displacement R = mean + w_factor xi (xi standard normal), which sets
+   * its fill vector gamma = fill_map R and its Husimi means (R restricted to modes 2..M).
+   * gamma and het_mean are then ignored. */
+  int mixed;
+  const double* mean;           /* 2M host: quadrature means R-bar */
+  const double* w_factor;       /* 2M x 2M host row-major: W = w_factor w_factor^T */
+  const gbsh_c128* fill_map;    /* M x 2M host row-major complex */
 } gbsh_sampler_cfg;
 
 typedef struct {

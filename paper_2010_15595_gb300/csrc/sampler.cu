@@ -73,7 +73,8 @@ double u53(uint32_t hi, uint32_t lo) {
 }
 
 // Stream layout of one chain: key = request seed; counter = (chain number, stream, index, 0).
-constexpr uint32_t kStreamNormals = 0, kStreamUniforms = 1;
+// Stream 2 draws the displacement of a mixed state's pure component (step 1).
+constexpr uint32_t kStreamNormals = 0, kStreamUniforms = 1, kStreamMixture = 2;
 
 void chain_words(uint64_t seed, uint32_t chain, uint32_t stream, uint32_t index, uint32_t out[4]) {
   const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
@@ -81,12 +82,13 @@ void chain_words(uint64_t seed, uint32_t chain, uint32_t stream, uint32_t index,
   philox4x32_10(ctr, key, out);
 }
 
-// 2*count standard normals by the Box-Muller transform, two per generator call.
-void chain_normals(uint64_t seed, uint32_t chain, int count2, double* z) {
+// `count2` standard normals of one stream by the Box-Muller transform, two per call.
+void chain_normals(uint64_t seed, uint32_t chain, int count2, double* z,
+                   uint32_t stream = kStreamNormals) {
   const double two_pi = 6.283185307179586476925286766559;
   for (int b = 0; 2 * b < count2; ++b) {
     uint32_t w[4];
-    chain_words(seed, chain, kStreamNormals, (uint32_t)b, w);
+    chain_words(seed, chain, stream, (uint32_t)b, w);
     const double u1 = u53(w[0], w[1]), u2 = u53(w[2], w[3]);
     const double r = std::sqrt(-2.0 * std::log(1.0 - u1));
     z[2 * b] = r * std::cos(two_pi * u2);
@@ -101,8 +103,9 @@ double chain_uniform(uint64_t seed, uint32_t chain, uint32_t k) {
 }
 
 // ------------------------------------------------------------------ fill-vector kernel
-// gam[c][i] = gbar[i] + sum_{j > k_c} B[i][j] conj(alpha_c[j]) for i <= k_c (one block per
-// chain; alpha_c is the chain's heterodyne outcome vector, entry 0 unused).
+// gam[c][i] = gbar_c[i] + sum_{j > k_c} B[i][j] conj(alpha_c[j]) for i <= k_c (one block per
+// chain; alpha_c is the chain's heterodyne outcome vector, entry 0 unused; gbar_c is the
+// fill vector of the chain's pure state, per slot).
 __global__ void sampler_gamma_kernel(const double2* __restrict__ B, int ldb,
                                      const double2* __restrict__ gbar,
                                      const double2* __restrict__ alpha, const int* __restrict__ slot,
@@ -112,6 +115,7 @@ __global__ void sampler_gamma_kernel(const double2* __restrict__ B, int ldb,
   if (c >= nchains) return;
   const int k = kk[c];
   const double2* a = alpha + (size_t)slot[c] * M;
+  const double2* gb = gbar + (size_t)slot[c] * M;
   double2* g = gam + (size_t)slot[c] * M;
   for (int i = threadIdx.x; i <= k; i += blockDim.x) {
     double re = 0.0, im = 0.0;
@@ -120,7 +124,7 @@ __global__ void sampler_gamma_kernel(const double2* __restrict__ B, int ldb,
       re = fma(b.x, x.x, fma(b.y, x.y, re));
       im = fma(b.y, x.x, fma(-b.x, x.y, im));
     }
-    g[i] = make_double2(gbar[i].x + re, gbar[i].y + im);
+    g[i] = make_double2(gb[i].x + re, gb[i].y + im);
   }
 }
 
@@ -156,6 +160,8 @@ struct gbsh_sampler {
   gbsh_sampler_cfg cfg{};
   std::vector<double2> B, gbar;
   std::vector<double> het_mean, het_chol;
+  std::vector<double> mix_mean, mix_wf;  // mixed states: R-bar (2M), W factor (2M x 2M)
+  std::vector<double2> fill_map;         // mixed states: M x 2M, fill vector = fill_map R
   int device = 0;
   // threading
   std::mutex mu;
@@ -341,8 +347,8 @@ void gbsh_sampler::run() {
   size_t mem_in_use = 0;  // estimate for the next tick of the admitted chains
   const int max_active = cfg.batching ? std::max(1, cfg.max_active) : 1;
   const int R = 2 * (cfg.M - 1);
-  std::vector<double> z(R), quad(R);
-  std::vector<double2> alpha_stage;
+  std::vector<double> z(R), quad(R), zmix, rdisp, hmean_stage;
+  std::vector<double2> alpha_stage, gbar_stage;
   while (rc == GBSH_OK) {
     {
       std::unique_lock<std::mutex> lk(mu);
@@ -374,9 +380,46 @@ void gbsh_sampler::run() {
       // Husimi distribution, staged and copied to their device slots
       for (size_t c = first_new; c < active.size(); ++c) {
         Chain& a = active[c];
+        const double* hmean = het_mean.data();
+        if (cfg.mixed) {
+          // step 1: displacement of this sample's pure component, R ~ N(R-bar, W); its fill
+          // vector fill_map R and Husimi means R restricted to modes 2..M
+          const int R2 = 2 * cfg.M;
+          zmix.resize(R2);
+          rdisp.resize(R2);
+          chain_normals(a.req->seed, a.chain_no, R2, zmix.data(), kStreamMixture);
+          for (int r = 0; r < R2; ++r) {
+            double acc = mix_mean[r];
+            for (int q = 0; q < R2; ++q) acc += mix_wf[(size_t)r * R2 + q] * zmix[q];
+            rdisp[r] = acc;
+          }
+          gbar_stage.assign(cfg.M, make_double2(0.0, 0.0));
+          for (int i = 0; i < cfg.M; ++i) {
+            double re = 0.0, im = 0.0;
+            for (int q = 0; q < R2; ++q) {
+              re += fill_map[(size_t)i * R2 + q].x * rdisp[q];
+              im += fill_map[(size_t)i * R2 + q].y * rdisp[q];
+            }
+            gbar_stage[i] = make_double2(re, im);
+          }
+          hmean_stage.resize(R);
+          for (int j = 1; j < cfg.M; ++j) {
+            hmean_stage[j - 1] = rdisp[j];
+            hmean_stage[(cfg.M - 1) + j - 1] = rdisp[cfg.M + j];
+          }
+          hmean = hmean_stage.data();
+        } else {
+          gbar_stage = gbar;
+        }
+        cudaError_t eg = cudaMemcpyAsync(dgbar + (size_t)a.slot * cfg.M, gbar_stage.data(),
+                                         sizeof(double2) * cfg.M, cudaMemcpyHostToDevice, st);
+        if (eg != cudaSuccess) {
+          rc = from_cuda(eg);
+          break;
+        }
         chain_normals(a.req->seed, a.chain_no, R, z.data());
         for (int r = 0; r < R; ++r) {
-          double acc = het_mean[r];
+          double acc = hmean[r];
           for (int q = 0; q <= r; ++q) acc += het_chol[(size_t)r * R + q] * z[q];
           quad[r] = acc;
         }
@@ -444,7 +487,8 @@ int gbsh_sampler_create(const gbsh_sampler_cfg* cfg, gbsh_sampler** out) {
   const int M = cfg->M;
   if (M < 1 || !cfg->B || cfg->ldb < M || !cfg->gamma || cfg->cutoff < 0 || cfg->cutoff > 16 ||
       cfg->n_cap < 0 || cfg->n_cap > GBSH_MAX_N || cfg->max_active < 1 ||
-      (M > 1 && (!cfg->het_mean || !cfg->het_chol)) ||
+      (M > 1 && !cfg->het_chol) || (M > 1 && !cfg->mixed && !cfg->het_mean) ||
+      (cfg->mixed && (!cfg->mean || !cfg->w_factor || !cfg->fill_map)) ||
       (cfg->precision != GBSH_PREC_FP64 && cfg->precision != GBSH_PREC_C32))
     return GBSH_EINVAL;
   std::unique_ptr<gbsh_sampler> h(new gbsh_sampler());
@@ -463,10 +507,22 @@ int gbsh_sampler_create(const gbsh_sampler_cfg* cfg, gbsh_sampler** out) {
                      cfg->het_mean ? cfg->het_mean + R : nullptr);
   h->het_chol.assign(cfg->het_chol ? cfg->het_chol : nullptr,
                      cfg->het_chol ? cfg->het_chol + (size_t)R * R : nullptr);
+  if (cfg->mixed) {
+    const int R2 = 2 * M;
+    h->mix_mean.assign(cfg->mean, cfg->mean + R2);
+    h->mix_wf.assign(cfg->w_factor, cfg->w_factor + (size_t)R2 * R2);
+    h->fill_map.resize((size_t)M * R2);
+    for (size_t i = 0; i < (size_t)M * R2; ++i)
+      h->fill_map[i] = make_double2(cfg->fill_map[i].re, cfg->fill_map[i].im);
+    h->het_mean.assign(R, 0.0);
+  }
   h->cfg.B = nullptr;
   h->cfg.gamma = nullptr;
   h->cfg.het_mean = nullptr;
   h->cfg.het_chol = nullptr;
+  h->cfg.mean = nullptr;
+  h->cfg.w_factor = nullptr;
+  h->cfg.fill_map = nullptr;
   const int slots = cfg->batching ? cfg->max_active : 1;
   h->free_slots.resize(slots);
   for (int i = 0; i < slots; ++i) h->free_slots[i] = slots - 1 - i;
@@ -482,14 +538,12 @@ int gbsh_sampler_create(const gbsh_sampler_cfg* cfg, gbsh_sampler** out) {
   };
   if ((e = cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking)) != cudaSuccess) return fail(e);
   if ((e = cudaMalloc(&h->dB, sizeof(double2) * M * M)) != cudaSuccess) return fail(e);
-  if ((e = cudaMalloc(&h->dgbar, sizeof(double2) * M)) != cudaSuccess) return fail(e);
+  if ((e = cudaMalloc(&h->dgbar, sizeof(double2) * (size_t)M * slots)) != cudaSuccess) return fail(e);
   if ((e = cudaMalloc(&h->dalpha, sizeof(double2) * (size_t)M * slots)) != cudaSuccess) return fail(e);
   if ((e = cudaMalloc(&h->dgam, sizeof(double2) * (size_t)M * slots)) != cudaSuccess) return fail(e);
   if ((e = cudaMalloc(&h->dslot, sizeof(int) * slots)) != cudaSuccess) return fail(e);
   if ((e = cudaMalloc(&h->dk, sizeof(int) * slots)) != cudaSuccess) return fail(e);
   if ((e = cudaMemcpy(h->dB, h->B.data(), sizeof(double2) * M * M, cudaMemcpyHostToDevice)) != cudaSuccess)
-    return fail(e);
-  if ((e = cudaMemcpy(h->dgbar, h->gbar.data(), sizeof(double2) * M, cudaMemcpyHostToDevice)) != cudaSuccess)
     return fail(e);
   cudaSetDevice(prev);
   gbsh_sampler* raw = h.release();

@@ -157,3 +157,40 @@ def test_chi_square_goodness_of_fit():
     sel = E >= 5
     chi2 = ((O[sel] - E[sel]) ** 2 / E[sel]).sum()
     assert stats.chi2.sf(chi2, sel.sum() - 1) > 1e-3, chi2
+
+
+def test_mixed_state_chi_square():
+    """Step 1 of Sec. III (Williamson split, displacement drawn from N(R-bar, W)): samples of
+    a lossy 3-mode state (transmission 0.6) against the exact mixed-state probabilities of
+    Eq. lhaf (2N-size loop hafnians, oracle)."""
+    import itertools
+    from scipy import stats
+    from paper_2010_15595_gb300 import sampler as S
+    m, n = 3, 200000
+    U, rv, al = _phys(m, 12, r=0.6, sigma=0.3)
+    V, R = S.lossy_state(U, rv, al, 0.6)
+    q = G.gbs_quantities(V, R)
+    pats = [p for p in itertools.product(range(7), repeat=m) if sum(p) <= 8]
+    probs = np.array([G.prob_mixed(q["A"], q["gamma"], q["pvac"], list(p)) for p in pats])
+    st = S.mixed_state(V, R)
+    with S.Sampler(st, cutoff=6, n_cap=60, max_active=4096) as smp:
+        out = np.concatenate(_run(smp, list(range(900, 920)), n_samples=n // 20))
+    base = 7 ** np.arange(m)
+    cnt = np.bincount((np.minimum(out, 6) * base).sum(1), minlength=7 ** m)
+    O = np.array([cnt[(np.array(p) * base).sum()] for p in pats], float)
+    E = probs * n
+    sel = E >= 5
+    chi2 = ((O[sel] - E[sel]) ** 2 / E[sel]).sum()
+    assert stats.chi2.sf(chi2, sel.sum() - 1) > 1e-3, chi2
+
+
+def test_pure_state_through_mixed_path_same_samples():
+    from paper_2010_15595_gb300 import sampler as S
+    U, rv, al = _phys(5, 13, r=0.6)
+    V, R = S.lossy_state(U, rv, al, 1.0)
+    with S.Sampler(S.pure_state(U, rv, al), cutoff=4, n_cap=40, max_active=64) as a:
+        pure = _run(a, range(16))
+    with S.Sampler(S.mixed_state(V, R), cutoff=4, n_cap=40, max_active=64) as b:
+        mixed = _run(b, range(16))
+    same = sum(np.array_equal(x, y) for x, y in zip(pure, mixed))
+    assert same >= 15  # equal up to a uniform falling within rounding of a CDF boundary

@@ -267,3 +267,13 @@ def test_single_mode_closed_forms():
     assert g[0] == pytest.approx(a)
     for n in range(6):
         assert G.prob_pure(B, g, pv, [n]) == pytest.approx(np.exp(-abs(a) ** 2) * abs(a) ** (2 * n) / _m.factorial(n), rel=1e-12)
+
+
+def test_mixed_form_thermal_closed_form():
+    """Eq. lhaf for a mixed state: single-mode thermal state, p(n) = nbar^n/(nbar+1)^(n+1)."""
+    from oracle import gbs as G
+    nbar = 0.7
+    q = G.gbs_quantities((2 * nbar + 1) * np.eye(2), np.zeros(2))
+    for n in range(6):
+        assert G.prob_mixed(q["A"], q["gamma"], q["pvac"], [n]) == pytest.approx(
+            nbar ** n / (nbar + 1) ** (n + 1), rel=1e-12)

@@ -83,3 +83,42 @@ def test_conditional_state_shortcut_matches_condV_condR():
         assert np.abs(Bk - B[np.ix_(A_modes, A_modes)]).max() < 1e-12
         shortcut = g[A_modes] + B[np.ix_(A_modes, B_modes)] @ np.conj(aB)
         assert np.abs(gk - shortcut).max() < 1e-12
+
+
+def _lossy(m, seed, eta):
+    from paper_2010_15595_gb300 import sampler as S
+    U, rv, al = _state(m, seed, r=0.5, sigma=0.3)
+    return S.lossy_state(U, rv, al, eta), (U, rv, al)
+
+
+@pytest.mark.parametrize("eta", [1.0, 0.6])
+def test_williamson_decomposition(eta):
+    """Eq. split: V = T + W with T = S^T S pure (S symplectic) and W >= 0."""
+    import torch
+    from paper_2010_15595_gb300 import sampler as S
+    (V, R), _ = _lossy(3, 4, eta)
+    Sm, nu = S.williamson(torch.from_numpy(V))
+    Sm, nu = Sm.numpy(), nu.numpy()
+    m = 3
+    Om = np.block([[np.zeros((m, m)), np.eye(m)], [-np.eye(m), np.zeros((m, m))]])
+    assert np.abs(Sm @ Om @ Sm.T - Om).max() < 1e-10
+    assert np.abs(Sm.T @ np.diag(np.concatenate([nu, nu])) @ Sm - V).max() < 1e-10
+    assert (nu >= 1 - 1e-10).all()
+    if eta == 1.0:
+        assert np.abs(nu - 1).max() < 1e-10
+    st = S.mixed_state(V, R, device="cpu")
+    W = st.w_factor @ st.w_factor.T
+    assert np.linalg.eigvalsh(W).min() > -1e-10
+
+
+def test_mixed_builder_reduces_to_pure_builder():
+    """For a pure state the mixture has W = 0, and the fill map at R-bar gives the pure
+    state's fill vector, with the same kernel matrix."""
+    from paper_2010_15595_gb300 import sampler as S
+    (V, R), (U, rv, al) = _lossy(4, 5, 1.0)
+    mx = S.mixed_state(V, R, device="cpu")
+    pu = S.pure_state(U, rv, al, device="cpu")
+    assert np.abs(mx.w_factor).max() < 1e-6
+    assert np.abs(mx.fill_map @ mx.mean - pu.gamma).max() < 1e-10
+    assert np.abs(mx.B - pu.B).max() < 1e-10
+    assert np.abs(mx.het_chol - pu.het_chol).max() < 1e-8
