@@ -156,3 +156,16 @@ def test_double_double_all_ones_telephone(gbsh):
         v = gbsh.lhaf_batch([W.all_ones(n)], precision=PREC_DD)[0]
         T = bench.telephone(n)
         assert float(abs(Fraction(v.real) - T) / T) <= 1e-13, (n, v, T)
+
+
+def test_autotuner_picks_a_candidate_and_keeps_results(gbsh, tmp_path, monkeypatch):
+    from paper_2010_15595_gb300 import autotune
+    monkeypatch.setenv("GBSH_TUNE_CACHE", str(tmp_path / "tune.json"))
+    mats = autotune.synthetic_batch(9, count=64, seed=3)
+    before = gbsh.lhaf_batch(mats)
+    res = autotune.tune_batch(9, count=64)
+    assert res["best"] in autotune.CANDIDATES and res["seconds"]
+    after = gbsh.lhaf_batch(mats)
+    assert np.array_equal(before, after)  # launch shape never changes the bits
+    assert autotune.apply_cache() == 1
+    gbsh.set_batch_tuning(0, 9, 0)
