@@ -526,7 +526,7 @@ def main(argv=None):
     p.add_argument("--serve-plain", type=int, default=6)
     p.add_argument("--serve-saturated", type=int, default=192)
     p.add_argument("--serve-slots", type=int, default=256)
-    p.add_argument("--serve-poisson", type=int, default=24)
+    p.add_argument("--serve-poisson", type=int, default=16)
     p.add_argument("--fig1", action="store_true",
                    help="run the Fig. 1 TVD experiment (Sec. III) instead of the benchmark")
     p.add_argument("--fig1-samples", type=int, default=200000)
