@@ -302,8 +302,9 @@ int gbsh_philox4x32(const uint32_t counter[4], const uint32_t key[2], uint32_t o
  * Sharing: all calls share the one array, which keeps the last call's contents (the call
  * clears what must start at zero). Calls whose GPU work may overlap -- on different
  * streams, or from different threads without ordering -- race on it; serialise them.
- * The launch plan is the library default (gbsh_set_lhaf_tuning does not apply), the same
- * chunking as gbsh_lhaf, so results agree with it.
+ * The launch plan is the library default (gbsh_set_lhaf_tuning does not apply), except
+ * that for large N the number of subset chunks is halved until the chunk partial sums fit
+ * the array; the result then agrees with gbsh_lhaf's to rounding, not bit for bit.
  * Errors: GBSH_EINVAL (N < 0, N > GBSH_MAX_N, lda < N, NULL pointers); GBSH_ENOMEM if an
  * evaluation would need more than GBSH_NOALLOC_SCRATCH_BYTES of scratch; GBSH_ECUDA.
  */

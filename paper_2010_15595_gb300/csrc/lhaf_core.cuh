@@ -19,6 +19,9 @@
 //   2. Reduce K' to upper Hessenberg form by stabilised elementary similarity
 //      transformations (Gaussian elimination with row pivoting), leaving index 0 fixed,
 //      so that the trailing m x m block stays similar to M. Half the flops of Householder.
+//      Each step also applies a diagonal similarity that makes the subdiagonal entry a
+//      power of two, so that La Budde's subdiagonal products are exact exponent shifts
+//      (no FP64 work). The column update of each step is spread over all 32 lanes.
 //   3. La Budde's recursion over the trailing principal submatrices, in "push" form (each
 //      finished polynomial is scattered into all later ones at once, lanes spread over
 //      (target, coefficient) pairs), truncated at degree n+1. It yields det(I - lambda M)
@@ -56,7 +59,8 @@ __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_dou
 // hardware approximation (rcp.approx.ftz.f64) and is refined by two Newton-Raphson steps
 // r <- r + r (1 - d r), each of which roughly doubles the number of correct bits; the
 // result is accurate to a few ulps (not correctly rounded), ample for a pivot reciprocal,
-// and costs 6 FP64 instructions instead of a full IEEE division.
+// and costs 8 FP64 instructions instead of a full IEEE division. It is applied to pivots
+// normalised to magnitude [1, 2 sqrt 2), so |a|^2 cannot underflow or overflow.
 __device__ __forceinline__ double2 crecip(double2 a) {
   const double d = fma(a.x, a.x, a.y * a.y);
   double r;
@@ -66,6 +70,24 @@ __device__ __forceinline__ double2 crecip(double2 a) {
   e = fma(-d, r, 1.0);
   r = fma(r, e, r);
   return make_double2(a.x * r, -a.y * r);
+}
+// x * 2^s, exact unless the result is subnormal. Integer instructions on the exponent field
+// when x and the result are normal (no FP64 issue); zero stays zero; subnormal inputs and
+// results outside the normal range go through ldexp.
+__device__ __forceinline__ double pow2_scale(double x, int s) {
+  const int hi = __double2hiint(x), lo = __double2loint(x);
+  const int ef = (hi >> 20) & 0x7ff;
+  if (ef != 0 && ef != 2047 && ef + s >= 1 && ef + s <= 2046)
+    return __hiloint2double((int)((unsigned)hi + ((unsigned)s << 20)), lo);
+  if (ef == 0 && ((hi & 0x000fffff) | lo) == 0) return x;  // +-0
+  return ldexp(x, s);
+}
+// Unbiased binary exponent of the larger component's magnitude (|a| in [2^E, 2^(E+1)*sqrt 2)).
+__device__ __forceinline__ int pow2_exponent(double2 a) {
+  const int ex = (__double2hiint(a.x) >> 20) & 0x7ff;
+  const int ey = (__double2hiint(a.y) >> 20) & 0x7ff;
+  const int eb = ex > ey ? ex : ey;
+  return (eb == 0 ? 1 : eb) - 1023;  // subnormals: scale as the smallest normal exponent
 }
 __device__ __forceinline__ double2 shfl_c(double2 v, int src) {
   return make_double2(__shfl_sync(FULL, v.x, src), __shfl_sync(FULL, v.y, src));
@@ -99,6 +121,11 @@ __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2
 __device__ __forceinline__ float2 crecip(float2 a) {
   const float inv = 1.0f / fmaf(a.x, a.x, a.y * a.y);
   return make_float2(a.x * inv, -a.y * inv);
+}
+__device__ __forceinline__ int pow2_exponent(float2 a) {
+  int e = 0;
+  frexpf(fmaxf(fabsf(a.x), fabsf(a.y)), &e);
+  return e - 1;
 }
 __device__ __forceinline__ float2 shfl_c(float2 v, int src) {
   return make_float2(__shfl_sync(FULL, v.x, src), __shfl_sync(FULL, v.y, src));
@@ -186,6 +213,7 @@ __device__ __forceinline__ ddc crecip(ddc a) {
   const dd r = dd_recip(a.x * a.x + a.y * a.y);
   return ddc{a.x * r, -(a.y * r)};
 }
+__device__ __forceinline__ int pow2_exponent(ddc a) { return pow2_exponent(make_double2(a.x.hi, a.y.hi)); }
 __device__ __forceinline__ dd shfl_d(dd v, int src) {
   return dd{__shfl_sync(FULL, v.hi, src), __shfl_sync(FULL, v.lo, src)};
 }
@@ -214,6 +242,9 @@ template <> struct Cx<double2> {
   __device__ __forceinline__ static double2 from(double2 v) { return v; }
   __device__ __forceinline__ static double2 to_d(double2 v) { return v; }
   __device__ __forceinline__ static Term to_term(double2 v) { return Term{v.x, 0.0, v.y, 0.0}; }
+  __device__ __forceinline__ static double2 scale2(double2 v, int s) {
+    return make_double2(pow2_scale(v.x, s), pow2_scale(v.y, s));
+  }
 };
 template <> struct Cx<ddc> {
   using R = dd;
@@ -223,6 +254,9 @@ template <> struct Cx<ddc> {
     return make_double2(v.x.hi + v.x.lo, v.y.hi + v.y.lo);
   }
   __device__ __forceinline__ static Term to_term(ddc v) { return Term{v.x.hi, v.x.lo, v.y.hi, v.y.lo}; }
+  __device__ __forceinline__ static ddc scale2(ddc v, int s) {
+    return ddc{dd{ldexp(v.x.hi, s), ldexp(v.x.lo, s)}, dd{ldexp(v.y.hi, s), ldexp(v.y.lo, s)}};
+  }
 };
 template <> struct Cx<float2> {
   using R = float;
@@ -232,6 +266,9 @@ template <> struct Cx<float2> {
   }
   __device__ __forceinline__ static double2 to_d(float2 v) { return make_double2(v.x, v.y); }
   __device__ __forceinline__ static Term to_term(float2 v) { return Term{v.x, 0.0, v.y, 0.0}; }
+  __device__ __forceinline__ static float2 scale2(float2 v, int s) {
+    return make_float2(ldexpf(v.x, s), ldexpf(v.y, s));
+  }
 };
 
 // 1/k for k = 0..63 (entry 0 unused), filled by the host with correctly rounded values.
@@ -266,6 +303,82 @@ struct DDAcc {
     abs_sum += fabs(t.re_hi) + fabs(t.im_hi);
   }
 };
+
+// Column c+1 of elimination step c of the Hessenberg reduction:
+//     H[r][c+1] <- f_r H[r][c+1] + sum_{i=c+2}^{S-1} H[r][i] H[i][c]   for every row r,
+// with f_r = piv except f_{c+1} = 1 (piv: the factor of the diagonal similarity of step c).
+// The S x Rr products are split evenly over the 32 lanes in row-major order, q per lane, so
+// one lane's range covers the tail of one row, possibly a whole row, and the head of another
+// (S <= 64 bounds it to three rows). Each lane runs one accumulator chain and parks the
+// partial of each row it finishes; the lane holding the first element of a row (its owner)
+// adds, in lane order, the head partials of the lanes that start inside that row, so the
+// rounding order is fixed. For short rows the plain one-lane-per-row loop issues fewer FP64
+// instructions and is used instead; the choice depends on (S, Rr) only, so it is uniform
+// across the warp.
+template <class T>
+__device__ __forceinline__ void column_update(T* __restrict__ H, int ldh, int S, int c, int Rr,
+                                              const T piv, const T one, int lane) {
+  using R = typename Cx<T>::R;
+  const T zero = Cx<T>::make(R(0), R(0));
+  const int passes = (S + 31) >> 5;
+  const int tot = S * Rr;
+  const int q = (tot + 31) >> 5;
+  const int G = Rr > 1 ? (Rr - 2 + q) / q : 0;  // lanes that can start inside one row
+  const bool seg = Rr > 0 && (4 * q + 2 * G + 4 * passes) < passes * (4 * Rr + 4);
+  if (!seg) {
+    for (int r = lane; r < S; r += 32) {
+      T acc = zero;
+      for (int i = c + 2; i < S; ++i) acc = cfma(acc, H[r * ldh + i], H[i * ldh + c]);
+      H[r * ldh + c + 1] = cfma(acc, r == c + 1 ? one : piv, H[r * ldh + c + 1]);
+    }
+    return;
+  }
+  const int e0 = lane * q;
+  const bool has = e0 < tot;
+  const int e1 = has ? min(e0 + q, tot) : e0;
+  const int ra = has ? e0 / Rr : 0;  // first row touched
+  const int o = has ? e0 - ra * Rr : 0;
+  // running partial `acc` of the current row; finished rows move to h0, h1
+  T acc = zero, h0 = zero, h1 = zero;
+  int nfl = 0;
+  int i = o;
+  const int cnt = e1 - e0;
+  const T* xr = H + ra * ldh + c + 2;
+  for (int t = 0; t < q; ++t) {
+    if (t < cnt) {
+      acc = cfma(acc, xr[i], H[(c + 2 + i) * ldh + c]);
+      if (++i == Rr) {
+        i = 0;
+        xr += ldh;
+        if (nfl == 0) h0 = acc; else h1 = acc;
+        ++nfl;
+        acc = zero;
+      }
+    }
+  }
+  const T a0 = nfl >= 1 ? h0 : acc;
+  const T a1 = nfl >= 2 ? h1 : (nfl == 1 ? acc : zero);
+  const T a2 = nfl >= 2 ? acc : zero;
+  const int rz = has ? (e1 - 1) / Rr : -1;  // last row touched
+  const int zs = rz - ra;
+  T tail = zs == 0 ? a0 : (zs == 1 ? a1 : a2);
+  const int ra_key = has ? ra : -1;
+  for (int j = 1; j <= G; ++j) {
+    const T nb = shfl_down_c(a0, (unsigned)j);
+    const int rj = __shfl_down_sync(FULL, ra_key, (unsigned)j);
+    if (has && lane + j < 32 && rj == rz) tail = cadd(tail, nb);
+  }
+  // rows owned: ra when the lane starts it, then the following rows that start in range
+  const int own1 = (o == 0) ? ra : ra + 1;
+  for (int w = 0; w < passes; ++w) {
+    const int r = own1 + w;
+    if (has && r <= rz) {
+      const int sl = r - ra;
+      const T v = (r == rz) ? tail : (sl == 0 ? a0 : (sl == 1 ? a1 : a2));
+      H[r * ldh + c + 1] = cfma(v, r == c + 1 ? one : piv, H[r * ldh + c + 1]);
+    }
+  }
+}
 
 // ------------------------------------------------------------------------------------
 // p_Z for subset z (bit j <=> pair (j, j+n) in Z) with k = popcount(z) >= 1.
@@ -320,8 +433,19 @@ __device__ __noinline__ Term subset_term_full(const Problem& P, uint64_t z, int 
   __syncwarp();
 
   // ---- 2. Hessenberg reduction by stabilised elementary similarities (index 0 fixed
-  //         automatically: column c only mixes rows/columns >= c+1).
-  for (int c = 0; c + 2 < S; ++c) {
+  //         automatically: column c only mixes rows/columns >= c+1), with subdiagonal
+  //         entries normalised to powers of two. At step c, after the row interchange, the
+  //         pivot pi = 2^E b with |b| in [1, 2 sqrt 2); the diagonal similarity that divides
+  //         row c+1 and multiplies column c+1 by b turns the pivot into 2^E, so the
+  //         multipliers are H[r][c] 2^-E (exact, integer instructions) and the only FP64
+  //         reciprocal is 1/b, which is well conditioned. The working matrix keeps its
+  //         natural scale; La Budde's subdiagonal products become powers of two, applied
+  //         afterwards without FP64 arithmetic. A column with nothing to eliminate (all
+  //         candidates zero) keeps a zero subdiagonal, recorded in `zmask`.
+  int* kexp = idx;  // the index list is no longer needed: exponent E of each subdiagonal
+  uint64_t zmask = 0;
+  for (int c = 0; c + 1 < S; ++c) {
+    const int Rr = S - c - 2;  // rows below the pivot row
     // pivot: largest magnitude in column c among rows c+1..S-1
     unsigned best = 0u;
     int brow = c + 1;
@@ -330,7 +454,11 @@ __device__ __noinline__ Term subset_term_full(const Problem& P, uint64_t z, int 
       if (mk > best) { best = mk; brow = r; }
     }
     unsigned mx = __reduce_max_sync(FULL, best);
-    if (mx == 0u) continue;  // column already zero below the subdiagonal
+    if (mx == 0u) {  // zero subdiagonal: nothing to eliminate or scale
+      zmask |= 1ull << c;
+      if (lane == 0) kexp[c] = 0;
+      continue;
+    }
     unsigned cand = __ballot_sync(FULL, best == mx);
     int p = __shfl_sync(FULL, brow, __ffs(cand) - 1);
     if (p != c + 1) {
@@ -347,83 +475,90 @@ __device__ __noinline__ Term subset_term_full(const Problem& P, uint64_t z, int 
       }
       __syncwarp();
     }
-    const T rinv = crecip(H[(c + 1) * ldh + c]);
-    // multipliers l_r = H[r][c] / pivot, kept in H[r][c] (below the subdiagonal)
-    for (int r = c + 2 + lane; r < S; r += 32) H[r * ldh + c] = cmul(H[r * ldh + c], rinv);
-    __syncwarp();
-    // rows r >= c+2:  H[r][j] -= l_r H[c+1][j],  j >= c+1
-    {
-      const int C = S - c - 1;
-      const int R = S - c - 2;
-      for (int e = lane; e < R * C; e += 32) {
-        int rr = e / C, jj = e - rr * C;
-        int r = c + 2 + rr, j = c + 1 + jj;
-        H[r * ldh + j] = cfms(H[r * ldh + j], H[r * ldh + c], H[(c + 1) * ldh + j]);
+    const T piv = H[(c + 1) * ldh + c];
+    const int E = pow2_exponent(piv);
+    const T bp = Cx<T>::scale2(piv, -E);  // pivot / 2^E
+    const T one = Cx<T>::make(R(1), R(0));
+    if (lane == 0) kexp[c] = E;
+    __syncwarp();  // every lane holds the pivot before its slot is reused below
+    if (Rr > 0) {
+      // scaled pivot row u_j = H[c+1][j] / b, j >= c+1. u_{c+1} is only an operand of the
+      // elimination (the diagonal entry itself is unchanged by the similarity) and is
+      // parked in the subdiagonal slot H[c+1][c], which is never read again.
+      const T rinv = crecip(bp);
+      for (int j = c + 1 + lane; j < S; j += 32) {
+        const T u = cmul(H[(c + 1) * ldh + j], rinv);
+        H[(c + 1) * ldh + (j == c + 1 ? c : j)] = u;
       }
+      // multipliers H[r][c] / 2^E, kept in column c below the subdiagonal
+      for (int r = c + 2 + lane; r < S; r += 32) H[r * ldh + c] = Cx<T>::scale2(H[r * ldh + c], -E);
+      __syncwarp();
+      // rows r >= c+2:  H[r][j] -= m_r u_j,  j >= c+1
+      {
+        const int C = Rr + 1;
+        for (int e = lane; e < Rr * C; e += 32) {
+          int rr = e / C, jj = e - rr * C;
+          int r = c + 2 + rr, j = c + 1 + jj;
+          const T u = H[(c + 1) * ldh + (jj == 0 ? c : j)];
+          H[r * ldh + j] = cfms(H[r * ldh + j], H[r * ldh + c], u);
+        }
+      }
+      __syncwarp();
     }
-    __syncwarp();
-    // column c+1 += sum_{i >= c+2} column i * l_i   (right multiplication by L^{-1})
-    for (int r = lane; r < S; r += 32) {
-      T acc = H[r * ldh + c + 1];
-      for (int i = c + 2; i < S; ++i) acc = cfma(acc, H[r * ldh + i], H[i * ldh + c]);
-      H[r * ldh + c + 1] = acc;
-    }
+    // column c+1 <- f_r H[r][c+1] + sum_{i >= c+2} H[r][i] m_i   (f_r = b, 1 at r = c+1)
+    column_update<T>(H, ldh, S, c, Rr, bp, one, lane);
     __syncwarp();
   }
-
-  // ---- 3a. C(a,b) = H[a][b] * prod_{l=a}^{b-1} H[l+1][l]  for a < b, in place.
-  {
-    T beta0 = Cx<T>::make(R(1), R(0)), beta1 = Cx<T>::make(R(1), R(0));
-    for (int b = 1; b < S; ++b) {
-      const T sub = H[b * ldh + b - 1];
-      if (lane < b) {
-        beta0 = cmul(beta0, sub);
-        H[lane * ldh + b] = cmul(H[lane * ldh + b], beta0);
-      }
-      if (lane + 32 < b) {
-        beta1 = cmul(beta1, sub);
-        H[(lane + 32) * ldh + b] = cmul(H[(lane + 32) * ldh + b], beta1);
-      }
+  // Subdiagonal l is 2^{E_l} (or zero, see zmask). La Budde needs H[a][b] times the product
+  // of the subdiagonals between rows a and b, i.e. H[a][b] 2^{K_b - K_a} with K the prefix
+  // sums of E: an exact rescaling of the strict upper triangle, integer-only when in range.
+  if (lane == 0) {
+    int acc = 0;
+    for (int l = 0; l < S; ++l) {
+      const int t = (l < S - 1) ? kexp[l] : 0;
+      kexp[l] = acc;
+      acc += t;
     }
   }
   __syncwarp();
+  for (int e = lane; e < S * S; e += 32) {
+    const int a = e / S, bb = e - a * S;
+    if (a < bb) H[a * ldh + bb] = Cx<T>::scale2(H[a * ldh + bb], kexp[bb] - kexp[a]);
+  }
+  __syncwarp();
 
-  // ---- 3b. La Budde over trailing blocks. P_t = det(I - lambda H[S-t.., S-t..]):
-  //   P_t = (1 - lambda H[a][a]) P_{t-1} - sum_{b=a+1}^{S-1} C(a,b) lambda^{b-a+1} P_{S-1-b},
-  //   a = S - t. Push form: when P_s is final, add its contribution to every P_t, t > s.
+  // ---- 3. La Budde over trailing blocks. With the subdiagonal products folded into the
+  //   upper triangle (H[a][b] now holds C(a,b) = H[a][b] prod_{l=a}^{b-1} H[l+1][l]), the
+  //   characteristic polynomials P_t = det(I - lambda H[S-t.., S-t..]) satisfy, for a = S-t,
+  //   P_t = P_{t-1} + Dl_t,  Dl_t = -lambda H[a][a] P_{t-1}
+  //                                 - sum_{b=a+1}^{S-1} C(a,b) lambda^{b-a+1} P_{S-1-b},
+  //   where a term is dropped when a zero subdiagonal lies between rows a and b.
+  //   Push form: once P_s is final it is scattered into every Dl_t, t > s (lanes spread
+  //   over (target, coefficient) pairs), after which P_{s+1} = P_s + Dl_{s+1} is final.
   for (int s = 0; s < S; ++s) {
     const T* Ps = Pl + poly_offset(s, D);
     const int degs = s < D ? s : D;  // P_s has degree <= s
-    // diagonal term into P_{s+1}: P_{s+1}[d] += P_s[d] - h P_s[d-1]
+    const int bcol = S - 1 - s;
     {
-      const int a = S - 1 - s;  // P_{s+1} starts at row a
-      const T h = H[a * ldh + a];
-      T* Pt = Pl + poly_offset(s + 1, D);
-      const int dmax = (s + 1) < D ? (s + 1) : D;
-      for (int d = lane; d <= dmax; d += 32) {
-        T acc = Pt[d];
-        if (d <= degs) acc = cadd(acc, Ps[d]);
-        if (d >= 1) acc = cfms(acc, h, Ps[d - 1]);
-        Pt[d] = acc;
-      }
-    }
-    // off-diagonal terms into P_t, t = s+2..S:  P_t[e + t - s] -= C(S-t, S-1-s) P_s[e]
-    {
-      const int nt = S - s - 1;                 // targets t = s+2 .. S
-      const int emax = (degs < D - 2) ? degs : D - 2;
-      if (nt > 0 && emax >= 0) {
-        const int ne = emax + 1;
-        const int bcol = S - 1 - s;
-        for (int f = lane; f < nt * ne; f += 32) {
-          int ti = f / ne, e = f - ti * ne;
-          int t = s + 2 + ti;
-          int d = e + t - s;
-          if (d <= D) {
-            T* Pt = Pl + poly_offset(t, D);
-            Pt[d] = cfms(Pt[d], H[(S - t) * ldh + bcol], Ps[e]);
-          }
+      const int nt = S - s;                            // targets t = s+1 .. S
+      const int ne = (degs < D - 1 ? degs : D - 1) + 1;
+      for (int f = lane; f < nt * ne; f += 32) {
+        const int ti = f / ne, e = f - ti * ne;
+        const int t = s + 1 + ti;
+        const int d = e + 1 + ti;
+        const int a = S - t;
+        const bool live = (d <= D) && ((zmask >> a) & ((1ull << ti) - 1ull)) == 0ull;
+        if (live) {
+          T* Pt = Pl + poly_offset(t, D);
+          Pt[d] = cfms(Pt[d], H[a * ldh + bcol], Ps[e]);
         }
       }
+    }
+    __syncwarp();
+    {
+      T* Pn = Pl + poly_offset(s + 1, D);
+      const int dmax = (s + 1) < D ? (s + 1) : D;
+      if (lane <= dmax && lane <= degs) Pn[lane] = cadd(Pn[lane], Ps[lane]);
     }
     __syncwarp();
   }

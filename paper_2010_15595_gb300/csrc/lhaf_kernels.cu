@@ -308,7 +308,8 @@ cudaError_t ensure_constants() {
   return cudaSuccess;
 }
 
-bool make_plan(int N, const DeviceInfo& dev, int warps_main, int kcap_override, LhafPlan* p) {
+bool make_plan(int N, const DeviceInfo& dev, int warps_main, int kcap_override, LhafPlan* p,
+               unsigned max_chunks) {
   if (N < 1 || N > kMaxN) return false;
   LhafPlan plan{};
   plan.N = N;
@@ -324,32 +325,27 @@ bool make_plan(int N, const DeviceInfo& dev, int warps_main, int kcap_override, 
       if ((size_t)W * area_bytes(k) <= limit) kc = k;
     return kc;
   };
-  int W = warps_main > 0 ? warps_main : 8;
+  int W = warps_main > 0 ? warps_main : 12;
   if (W > kMaxWarps) W = kMaxWarps;
-  // Popcount classes with decreasing warps per CTA: most subsets (popcount near n/2) run
-  // with W warps; the few large ones run in launches whose warps have larger work areas.
+  // Popcount classes: subsets with popcount in (k_prev, k_c] run in one launch with W_c warps
+  // per CTA, W_c the largest count of a fixed ladder (capped at W) whose work areas fit.
+  // Most subsets (popcount near n/2) have small matrices and run with many warps per SM to
+  // hide the FP64 latency; the few large ones run with larger work areas.
+  static const int kLadder[] = {16, 12, 8, 6, 4, 3, 2, 1};
   plan.nclass = 0;
   int k_done = 0;
-  int kc = kfit(W);
-  if (kcap_override > 0 && kcap_override < kc) kc = kcap_override;
-  if (kc >= 1) {
-    plan.cls[plan.nclass++] = ClassPlan{1, kc, W, warp_area_elems(kc, n), 0};
-    k_done = kc;
-  }
-  if (k_done < n && W > 4) {
-    const int W2 = W / 2 > 4 ? W / 2 : 4;
-    const int kc2 = kfit(W2);
-    if (kc2 > k_done && kc2 < n) {
-      plan.cls[plan.nclass++] = ClassPlan{k_done + 1, kc2, W2, warp_area_elems(kc2, n), 0};
-      k_done = kc2;
+  for (int wi = 0; wi < (int)(sizeof(kLadder) / sizeof(kLadder[0])) && k_done < n; ++wi) {
+    const int Wc = kLadder[wi];
+    if (Wc > W) continue;
+    int kc = kfit(Wc);
+    if (plan.nclass == 0 && kcap_override > 0 && kcap_override < kc) kc = kcap_override;
+    if (kc > k_done) {
+      if (plan.nclass == kMaxClasses) return false;
+      plan.cls[plan.nclass++] = ClassPlan{k_done + 1, kc, Wc, warp_area_elems(kc, n), 0};
+      k_done = kc;
     }
   }
-  if (k_done < n) {
-    int W3 = (int)(limit / area_bytes(n));
-    if (W3 < 1) return false;
-    if (W3 > W) W3 = W;
-    plan.cls[plan.nclass++] = ClassPlan{k_done + 1, n, W3, warp_area_elems(n, n), 0};
-  }
+  if (k_done < n) return false;
   for (int c = 0; c < plan.nclass; ++c) {
     ClassPlan& cp = plan.cls[c];
     int per_sm = 0;
@@ -361,12 +357,14 @@ bool make_plan(int N, const DeviceInfo& dev, int warps_main, int kcap_override, 
     cp.blocks = per_sm * dev.sm_count;
   }
   const uint64_t total = (uint64_t)1 << n;
-  plan.nchunks = (unsigned)(total < kTargetChunks ? total : kTargetChunks);
+  unsigned cap = kTargetChunks;  // largest power of two <= max_chunks
+  while (cap > 1u && cap > max_chunks) cap >>= 1;
+  plan.nchunks = (unsigned)(total < cap ? total : cap);
   plan.chunk_size = total / plan.nchunks;
   size_t off = 0;
   plan.off_A0 = off; off = align256(off + sizeof(double2) * plan.Ne * plan.Ne);
   plan.off_v = off; off = align256(off + sizeof(double2) * plan.Ne);
-  plan.off_partials = off; off = align256(off + sizeof(double) * 5 * (size_t)kMaxClasses * plan.nchunks);
+  plan.off_partials = off; off = align256(off + sizeof(double) * 5 * (size_t)plan.nclass * plan.nchunks);
   plan.off_counters = off; off = align256(off + sizeof(unsigned) * kMaxClasses);
   plan.off_out = off; off = align256(off + sizeof(double) * 4);
   plan.bytes = off;
@@ -397,6 +395,31 @@ static cudaError_t launch_expand(const LhafPlan& plan, const double2* base, int 
   return cudaGetLastError();
 }
 
+// Side streams on which the popcount classes after the first run, so that the tail of one
+// class launch overlaps the next (each class has its own counter and partial sums). One set
+// per device, created on first use and kept for the life of the process.
+static cudaError_t side_streams(cudaStream_t** out) {
+  static cudaStream_t streams[64][kMaxClasses] = {};
+  static bool made[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!made[dev]) {
+    for (int c = 1; c < kMaxClasses; ++c) {
+      e = cudaStreamCreateWithFlags(&streams[dev][c], cudaStreamNonBlocking);
+      if (e != cudaSuccess) return e;
+    }
+    made[dev] = true;
+  }
+  *out = streams[dev];
+  return cudaSuccess;
+}
+
+// Launches every popcount class. Class 0 runs on `stream`; the others on the side streams,
+// forked from and joined back into `stream` with events, so all work of the evaluation is
+// ordered after what precedes it on `stream` and before what follows.
 template <bool kVisit>
 static cudaError_t launch_classes(const LhafPlan& plan, void* ws, unsigned* visits,
                                   cudaStream_t stream) {
@@ -406,16 +429,35 @@ static cudaError_t launch_classes(const LhafPlan& plan, void* ws, unsigned* visi
   cudaError_t e = cudaMemsetAsync(counters, 0, sizeof(unsigned) * kMaxClasses, stream);
   if (e != cudaSuccess) return e;
   const Problem P = problem_of(plan, ws);
-  for (int c = 0; c < plan.nclass; ++c) {
+  cudaStream_t* side = nullptr;
+  cudaEvent_t fork = nullptr;
+  if (plan.nclass > 1) {
+    e = side_streams(&side);
+    if (e != cudaSuccess) return e;
+    e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+    e = cudaEventRecord(fork, stream);
+  }
+  for (int c = 0; c < plan.nclass && e == cudaSuccess; ++c) {
     const ClassPlan& cp = plan.cls[c];
+    cudaStream_t sc = c == 0 ? stream : side[c];
+    if (c > 0) e = cudaStreamWaitEvent(sc, fork, 0);
+    if (e != cudaSuccess) break;
     size_t smem = (size_t)cp.warps * cp.area_elems * sizeof(double2);
-    lhaf_subsets_kernel<kVisit><<<cp.blocks, 32 * cp.warps, smem, stream>>>(
+    lhaf_subsets_kernel<kVisit><<<cp.blocks, 32 * cp.warps, smem, sc>>>(
         P, cp.k_lo, cp.k_hi, cp.area_elems, plan.chunk_size, plan.nchunks, counters + c,
         partials + (size_t)c * plan.nchunks * 5, visits);
     e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    if (e == cudaSuccess && c > 0) {
+      cudaEvent_t join = nullptr;
+      e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventRecord(join, sc);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, join, 0);
+      if (join) cudaEventDestroy(join);
+    }
   }
-  return cudaSuccess;
+  if (fork) cudaEventDestroy(fork);
+  return e;
 }
 
 cudaError_t launch_lhaf(const LhafPlan& plan, const double2* base, int ld, const double2* diag,

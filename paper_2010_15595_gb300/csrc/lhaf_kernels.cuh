@@ -11,8 +11,8 @@ namespace gbsh {
 
 constexpr int kMaxWarps = 16;          // warps per CTA of the subset kernel
 constexpr int kFinalizeThreads = 256;  // threads of the finalize kernel
-constexpr int kMaxClasses = 3;         // popcount classes of one evaluation
-constexpr unsigned kTargetChunks = 1u << 16;
+constexpr int kMaxClasses = 8;         // popcount classes of one evaluation
+constexpr unsigned kTargetChunks = 1u << 18;  // Gray-code chunks of one evaluation (at most)
 
 // One launch of the subset kernel: subsets with popcount in [k_lo, k_hi], `warps` warps per
 // CTA, each warp owning `area_elems` double2 of shared memory.
@@ -40,9 +40,11 @@ struct DeviceInfo {
 cudaError_t device_info(DeviceInfo* info);
 // Uploads constant tables on the current device (once per device).
 cudaError_t ensure_constants();
-// Builds the launch plan. warps_main = 0 selects the default. Returns false if N is out of
-// range for the available shared memory.
-bool make_plan(int N, const DeviceInfo& dev, int warps_main, int kcap_override, LhafPlan* plan);
+// Builds the launch plan. warps_main = 0 selects the default cap on warps per CTA;
+// max_chunks bounds the number of subset chunks (a power of two). Returns false if N is out
+// of range for the available shared memory.
+bool make_plan(int N, const DeviceInfo& dev, int warps_main, int kcap_override, LhafPlan* plan,
+               unsigned max_chunks = kTargetChunks);
 
 // Launches expansion + subset classes + finalize for one problem. `base`, `diag`, `idx` as
 // in expand_problem_kernel. Writes lhaf (re, im) and sum |p_Z| into ws + off_out.

@@ -76,9 +76,15 @@ int gbsh_lhaf_noalloc(const gbsh_c128* dA, int N, int lda, gbsh_c128* d_out, dou
   if (e != cudaSuccess) return fail(e);
   e = gbsh::ensure_constants();
   if (e != cudaSuccess) return fail(e);
+  // The library default plan, with the chunk count halved until the scratch fits.
   gbsh::LhafPlan plan;
-  if (!gbsh::make_plan(N, info, 0, 0, &plan)) return GBSH_EINVAL;
-  if (plan.bytes > (size_t)GBSH_NOALLOC_SCRATCH_BYTES) return GBSH_ENOMEM;
+  unsigned max_chunks = gbsh::kTargetChunks;
+  for (;;) {
+    if (!gbsh::make_plan(N, info, 0, 0, &plan, max_chunks)) return GBSH_EINVAL;
+    if (plan.bytes <= (size_t)GBSH_NOALLOC_SCRATCH_BYTES) break;
+    if (plan.nchunks <= 1u) return GBSH_ENOMEM;
+    max_chunks = plan.nchunks / 2;
+  }
 
   // The chunk counters are zeroed inside launch_lhaf; every other scratch byte the
   // kernels read is written earlier in the same launch sequence.

@@ -111,6 +111,17 @@ def test_c32_variant_error_map(gbsh):
     assert np.array_equal(mixed[ns:], f64[ns:])
 
 
+def test_c32_finite_at_batched_workload_sizes(gbsh):
+    """The complex-FP32 variant stays finite across the batched workload's sizes (N = 10..30):
+    pivots are running products whose squares would leave FP32's exponent range without the
+    power-of-two pre-scaling in the complex reciprocal."""
+    from paper_2010_15595_gb300.lib import PREC_C32
+    B, gamma = W.batch_state()
+    mats = [G.expand_pure(B, gamma, p) for p in W.batch_patterns(48, seed=13, n_min=10, n_max=30)]
+    c32 = gbsh.lhaf_batch(mats, precision=PREC_C32)
+    assert np.all(np.isfinite(c32.real)) and np.all(np.isfinite(c32.imag))
+
+
 def test_batch_rejects_bad_input(gbsh):
     with pytest.raises(gbsh.GbshError):
         gbsh.lhaf_batch([np.ones((61, 61), complex)])

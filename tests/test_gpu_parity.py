@@ -54,6 +54,21 @@ def test_random_small_vs_definition(gbsh, N):
     assert rel(got, ref) <= fp64_tol(N, ref, sq), (N, got, ref)
 
 
+@pytest.mark.parametrize("scale", [1e-9, 1e9])
+def test_extreme_entry_scale(gbsh, scale):
+    """The unit-subdiagonal Hessenberg reduction makes each pivot a running product of the
+    earlier ones, so at N = 24 with entries near 1e-9 (1e9) |pivot|^2 would leave the double
+    exponent range; the complex reciprocal pre-scales by a power of two. Against the
+    definition (subset DP)."""
+    rng = np.random.default_rng(77)
+    A = W.random_complex_symmetric(24, rng) * scale
+    ref = L.lhaf_dp(A)
+    got = gbsh.lhaf(_dev(A))
+    _, _, sq = L.lhaf_subset_stats(A)
+    assert np.isfinite(got.real) and np.isfinite(got.imag)
+    assert rel(got, ref) <= fp64_tol(24, ref, sq), (scale, got, ref)
+
+
 @pytest.mark.parametrize("N", [1, 2, 3, 8, 15, 22, 29, 30])
 def test_all_ones(gbsh, N):
     """lhaf(all-ones) = telephone number T(N)."""
