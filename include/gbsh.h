@@ -151,6 +151,18 @@ int gbsh_gbs_prob_batch(const gbsh_c128* B, int M, int ldb, const gbsh_c128* gam
  * pairs (N = 2 n_max), per precision (0 = built-in default). Set by the autotuner. */
 int gbsh_set_batch_tuning(int precision, int n_max, int warps_per_cta);
 
+/* CUDA-graph replay of the batched evaluations (gbsh_lhaf_batch, gbsh_gbs_prob_batch and the
+ * sampler's ticks). The device work of one batched evaluation -- expansion, the persistent
+ * popcount-class launches, the finalize -- is captured into a CUDA graph the second time the
+ * same launch shape is seen (same device, workspace layout and addresses, problem count,
+ * chunk total, largest size, precision and warps per CTA) and replayed with one graph launch
+ * from then on; the
+ * per-call tables are uploaded before the launch. Results are bit-identical to direct
+ * launches. enable = 1 (the default) or 0. Returns GBSH_OK. */
+int gbsh_set_batch_graphs(int enable);
+/* Process-wide counts of graphs captured and of graph launches by the batched path. */
+int gbsh_batch_graph_stats(long long* captures, long long* replays);
+
 /*
  * gbsh_gbs_prob — pure-state GBS probability, Eq. lhaf-pure (Sec. II):
  *   p(S) = p_vac * |lhaf(filldiag(B_S, gamma_S))|^2 / prod_i s_i!
@@ -200,7 +212,7 @@ int gbsh_set_lhaf_tuning(int warps_per_cta, int kcap);
  * gbsh_lhaf_plan — launch plan that gbsh_lhaf / gbsh_lhaf_async use for size N on the
  * current device, under the current tuning. Any output pointer may be NULL.
  *   nclass     number of subset-kernel launches (popcount classes, 1..3)
- *   kernels    CUDA kernels launched per evaluation (expansion + classes + finalize)
+ *   kernels    CUDA kernels launched per evaluation (expansion + classes + two-level finalize)
  *   warps      warps per CTA of the first class
  *   kcap       largest popcount of the first class
  *   nchunks    number of fixed subset chunks (the reduction order depends only on this)

@@ -1,6 +1,9 @@
 // Host helpers of the batched evaluation (see batch_host.h).
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 #include <numeric>
+#include <vector>
 
 #include "batch_host.h"
 #include "lhaf_kernels.cuh"
@@ -9,7 +12,119 @@ namespace gbsh {
 
 namespace {
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// ---- CUDA-graph replay of the device part of a batched evaluation.
+// The device work of batch_run (expansion, the popcount-class launches, finalize) depends on
+// its inputs only through the workspace contents, which are uploaded before it, and through
+// the launch shape: the device addresses its kernels are given (tables, counters, partial
+// sums, results; they move with the caller's staged bytes and the batch's size mix), problem
+// count, chunk total, n_max, precision and warps per CTA. A shape seen a second time is
+// captured once into a graph (on a private
+// stream, with a private side stream for the second class) and replayed with
+// cudaGraphLaunch from then on; graph and direct launches run the same kernels with the same
+// arguments, so results are bit-identical.
+struct GraphKey {
+  int dev, count, n_max, precision, warps;
+  unsigned total_chunks;
+  const char *in, *prob, *counter, *partials, *out;
+  bool operator==(const GraphKey& o) const {
+    return dev == o.dev && count == o.count && n_max == o.n_max && precision == o.precision &&
+           warps == o.warps && total_chunks == o.total_chunks && in == o.in && prob == o.prob &&
+           counter == o.counter && partials == o.partials && out == o.out;
+  }
+};
+struct GraphEntry {
+  GraphKey key;
+  cudaGraphExec_t exec;
+  unsigned long long last_use;
+};
+constexpr size_t kMaxGraphs = 8;     // instantiated graphs kept (least recently used evicted)
+constexpr size_t kMaxSeenKeys = 64;  // shapes seen once (captured on their second use)
+std::mutex g_graph_mu;
+std::vector<GraphEntry> g_graphs;
+std::vector<GraphKey> g_seen;
+unsigned long long g_clock = 0;
+std::atomic<bool> g_graphs_enabled{true};
+std::atomic<long long> g_captures{0}, g_replays{0};
+cudaStream_t g_cap_stream[64] = {}, g_cap_side[64] = {};
+
+// Returns the exec for `key` (nullptr if none yet); records first sightings.
+cudaGraphExec_t graph_lookup(const GraphKey& key, bool* capture_now) {
+  std::lock_guard<std::mutex> lk(g_graph_mu);
+  *capture_now = false;
+  for (GraphEntry& g : g_graphs)
+    if (g.key == key) {
+      g.last_use = ++g_clock;
+      return g.exec;
+    }
+  for (const GraphKey& k : g_seen)
+    if (k == key) {
+      *capture_now = true;
+      return nullptr;
+    }
+  if (g_seen.size() >= kMaxSeenKeys) g_seen.erase(g_seen.begin());
+  g_seen.push_back(key);
+  return nullptr;
+}
+
+void graph_store(const GraphKey& key, cudaGraphExec_t exec) {
+  std::lock_guard<std::mutex> lk(g_graph_mu);
+  if (g_graphs.size() >= kMaxGraphs) {
+    auto lru = std::min_element(g_graphs.begin(), g_graphs.end(),
+                                [](const GraphEntry& a, const GraphEntry& b) {
+                                  return a.last_use < b.last_use;
+                                });
+    cudaGraphExecDestroy(lru->exec);
+    g_graphs.erase(lru);
+  }
+  g_graphs.push_back(GraphEntry{key, exec, ++g_clock});
+}
+
+// Captures launch_batch for `key` into an executable graph (nullptr on any failure: the
+// caller then launches directly).
+cudaGraphExec_t graph_capture(const GraphKey& key, const BatchLayout& L, char* w, int count,
+                              int precision, int W) {
+  if (key.dev < 0 || key.dev >= 64) return nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    if (!g_cap_stream[key.dev]) {
+      if (cudaStreamCreateWithFlags(&g_cap_stream[key.dev], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaStreamCreateWithFlags(&g_cap_side[key.dev], cudaStreamNonBlocking) != cudaSuccess)
+        return nullptr;
+    }
+  }
+  cudaStream_t cs = g_cap_stream[key.dev];
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return nullptr;
+  cudaError_t e = launch_batch(reinterpret_cast<const BatchInput*>(w + L.off_in),
+                               reinterpret_cast<const BatchProblem*>(w + L.off_prob), count,
+                               L.total_chunks, L.n_max, precision, W,
+                               reinterpret_cast<unsigned*>(w + L.off_counter),
+                               reinterpret_cast<double*>(w + L.off_partials),
+                               reinterpret_cast<double*>(w + L.off_out), cs, g_cap_side[key.dev]);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+  if (e != cudaSuccess || e2 != cudaSuccess || !graph) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return nullptr;
+  }
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  g_captures.fetch_add(1);
+  return exec;
+}
 }  // namespace
+
+void set_batch_graphs(bool enable) { g_graphs_enabled.store(enable); }
+void batch_graph_stats(long long* captures, long long* replays) {
+  if (captures) *captures = g_captures.load();
+  if (replays) *replays = g_replays.load();
+}
 
 BatchLayout batch_layout(const int* Ns, int count, size_t base_off) {
   BatchLayout L;
@@ -40,8 +155,8 @@ BatchLayout batch_layout(const int* Ns, int count, size_t base_off) {
   L.off_in = off; off = align_up(off + sizeof(BatchInput) * count);
   L.off_prob = off; off = align_up(off + sizeof(BatchProblem) * count);
   L.off_expanded = off; off = align_up(off + sizeof(double2) * exp_elems);
-  L.off_partials = off; off = align_up(off + sizeof(double) * 5 * (size_t)L.total_chunks);
-  L.off_counter = off; off = align_up(off + sizeof(unsigned));
+  L.off_partials = off; off = align_up(off + sizeof(double) * 5 * 2 * (size_t)L.total_chunks);
+  L.off_counter = off; off = align_up(off + sizeof(unsigned) * 2);
   L.off_out = off; off = align_up(off + sizeof(double) * 3 * (size_t)count);
   L.bytes = off;
   return L;
@@ -73,11 +188,30 @@ cudaError_t batch_run(BatchLayout& L, const std::vector<BatchInput>& in, int cou
   if (e != cudaSuccess) return e;
   const int W = batch_warps_for(std::max(L.n_max, 1), precision, dev, warps_pref);
   if (W < 1) return cudaErrorInvalidValue;
-  e = launch_batch(reinterpret_cast<const BatchInput*>(w + L.off_in),
-                   reinterpret_cast<const BatchProblem*>(w + L.off_prob), count, L.total_chunks,
-                   L.n_max, precision, W, reinterpret_cast<unsigned*>(w + L.off_counter),
-                   reinterpret_cast<double*>(w + L.off_partials),
-                   reinterpret_cast<double*>(w + L.off_out), st);
+  cudaGraphExec_t exec = nullptr;
+  if (g_graphs_enabled.load() && count > 0) {
+    int d = 0;
+    e = cudaGetDevice(&d);
+    if (e != cudaSuccess) return e;
+    const GraphKey key{d, count, L.n_max, precision, W, L.total_chunks, w + L.off_in,
+                       w + L.off_prob, w + L.off_counter, w + L.off_partials, w + L.off_out};
+    bool capture_now = false;
+    exec = graph_lookup(key, &capture_now);
+    if (!exec && capture_now) {
+      exec = graph_capture(key, L, w, count, precision, W);
+      if (exec) graph_store(key, exec);
+    }
+  }
+  if (exec) {
+    e = cudaGraphLaunch(exec, st);
+    if (e == cudaSuccess) g_replays.fetch_add(1);
+  } else {
+    e = launch_batch(reinterpret_cast<const BatchInput*>(w + L.off_in),
+                     reinterpret_cast<const BatchProblem*>(w + L.off_prob), count, L.total_chunks,
+                     L.n_max, precision, W, reinterpret_cast<unsigned*>(w + L.off_counter),
+                     reinterpret_cast<double*>(w + L.off_partials),
+                     reinterpret_cast<double*>(w + L.off_out), st);
+  }
   if (e != cudaSuccess) return e;
   std::vector<double> res(3 * (size_t)count);
   e = cudaMemcpyAsync(res.data(), w + L.off_out, sizeof(double) * res.size(),

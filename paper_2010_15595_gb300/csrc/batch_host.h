@@ -31,4 +31,9 @@ BatchLayout batch_layout(const int* Ns, int count, size_t base_off);
 cudaError_t batch_run(BatchLayout& L, const std::vector<BatchInput>& in, int count, int precision,
                       int warps_pref, void* ws, cudaStream_t st, double* out3);
 
+// CUDA-graph replay of batch_run's device work for launch shapes seen before (on by default).
+void set_batch_graphs(bool enable);
+// Graphs captured and graph launches so far (process-wide).
+void batch_graph_stats(long long* captures, long long* replays);
+
 }  // namespace gbsh

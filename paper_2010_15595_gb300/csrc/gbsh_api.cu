@@ -206,7 +206,7 @@ int gbsh_lhaf_plan(int N, int* nclass, int* kernels, int* warps, int* kcap, int*
   int rc = plan_for(N, &plan);
   if (rc != GBSH_OK) return rc;
   if (nclass) *nclass = plan.nclass;
-  if (kernels) *kernels = plan.nclass + 2;
+  if (kernels) *kernels = plan.nclass + 3;
   if (warps) *warps = plan.cls[0].warps;
   if (kcap) *kcap = plan.cls[0].k_hi;
   if (nchunks) *nchunks = (int)plan.nchunks;
@@ -508,6 +508,16 @@ int gbsh_set_batch_tuning(int precision, int n_max, int warps_per_cta) {
     return GBSH_EINVAL;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_batch_warps[precision][n_max] = warps_per_cta;
+  return GBSH_OK;
+}
+
+int gbsh_set_batch_graphs(int enable) {
+  gbsh::set_batch_graphs(enable != 0);
+  return GBSH_OK;
+}
+
+int gbsh_batch_graph_stats(long long* captures, long long* replays) {
+  gbsh::batch_graph_stats(captures, replays);
   return GBSH_OK;
 }
 

@@ -105,25 +105,22 @@ subset_terms_kernel(Problem P, int area_elems, const uint64_t* __restrict__ zs, 
 }
 
 // ------------------------------------------------------------------ finalize
-// Sums partials[cls][ch][5] over cls < nclass and ch < nchunks in a fixed order.
-// out[0..1] = lhaf (re, im), out[2] = sum over subsets of |Re p_Z| + |Im p_Z|.
-__global__ void __launch_bounds__(kFinalizeThreads)
-lhaf_finalize_kernel(const double* __restrict__ partials, unsigned nchunks, int nclass,
-                     double* __restrict__ out) {
-  __shared__ double sh[5][kFinalizeThreads];
+// Two levels, both in a fixed order (results do not depend on scheduling):
+//   lhaf_partials_kernel: CTA b sums chunks [b*per, (b+1)*per) of every class into
+//     block_out[b][5] (per = ceil(nchunks / gridDim.x));
+//   lhaf_finalize_kernel: one CTA sums block_out[0..nblocks) in block order into
+//     out[0..1] = lhaf (re, im), out[2] = sum over subsets of |Re p_Z| + |Im p_Z|.
+// Each level: thread-strided compensated sums, then a fixed binary tree in shared memory.
+__device__ __forceinline__ void add_partial(DDAcc& a, const double* __restrict__ q) {
+  double s, e;
+  DDAcc::two_sum(a.re_hi, q[0], s, e); a.re_hi = s; a.re_lo += e + q[1];
+  DDAcc::two_sum(a.im_hi, q[2], s, e); a.im_hi = s; a.im_lo += e + q[3];
+  a.abs_sum += q[4];
+}
+
+// Tree over the CTA's threads; the CTA total ends in sh[.][0].
+__device__ __forceinline__ void block_tree(DDAcc a, double (*sh)[kFinalizeThreads]) {
   const int t = threadIdx.x;
-  DDAcc a;
-  a.zero();
-  for (int cls = 0; cls < nclass; ++cls) {
-    const double* p = partials + (size_t)cls * nchunks * 5;
-    for (unsigned ch = t; ch < nchunks; ch += kFinalizeThreads) {
-      const double* q = p + (size_t)ch * 5;
-      double s, e;
-      DDAcc::two_sum(a.re_hi, q[0], s, e); a.re_hi = s; a.re_lo += e + q[1];
-      DDAcc::two_sum(a.im_hi, q[2], s, e); a.im_hi = s; a.im_lo += e + q[3];
-      a.abs_sum += q[4];
-    }
-  }
   sh[0][t] = a.re_hi; sh[1][t] = a.re_lo; sh[2][t] = a.im_hi; sh[3][t] = a.im_lo; sh[4][t] = a.abs_sum;
   __syncthreads();
   for (int w = kFinalizeThreads / 2; w > 0; w >>= 1) {
@@ -135,7 +132,34 @@ lhaf_finalize_kernel(const double* __restrict__ partials, unsigned nchunks, int 
     }
     __syncthreads();
   }
-  if (t == 0) {
+}
+
+__global__ void __launch_bounds__(kFinalizeThreads)
+lhaf_partials_kernel(const double* __restrict__ partials, unsigned nchunks, int nclass,
+                     double* __restrict__ block_out) {
+  __shared__ double sh[5][kFinalizeThreads];
+  const unsigned per = (nchunks + gridDim.x - 1) / gridDim.x;
+  const unsigned c0 = blockIdx.x * per;
+  const unsigned c1 = c0 + per < nchunks ? c0 + per : nchunks;
+  DDAcc a;
+  a.zero();
+  for (int cls = 0; cls < nclass; ++cls) {
+    const double* p = partials + (size_t)cls * nchunks * 5;
+    for (unsigned ch = c0 + threadIdx.x; ch < c1; ch += kFinalizeThreads) add_partial(a, p + (size_t)ch * 5);
+  }
+  block_tree(a, sh);
+  if (threadIdx.x == 0)
+    for (int j = 0; j < 5; ++j) block_out[(size_t)blockIdx.x * 5 + j] = sh[j][0];
+}
+
+__global__ void __launch_bounds__(kFinalizeThreads)
+lhaf_finalize_kernel(const double* __restrict__ block_out, int nblocks, double* __restrict__ out) {
+  __shared__ double sh[5][kFinalizeThreads];
+  DDAcc a;
+  a.zero();
+  for (int b = threadIdx.x; b < nblocks; b += kFinalizeThreads) add_partial(a, block_out + (size_t)b * 5);
+  block_tree(a, sh);
+  if (threadIdx.x == 0) {
     out[0] = sh[0][0] + sh[1][0];
     out[1] = sh[2][0] + sh[3][0];
     out[2] = sh[4][0];
@@ -181,7 +205,7 @@ __global__ void expand_batch_kernel(const BatchInput* __restrict__ in,
 template <class T>
 __global__ void __launch_bounds__(32 * kMaxWarps, 1)
 lhaf_batch_kernel(const BatchProblem* __restrict__ prob, int count, unsigned total_chunks,
-                  int area_elems, unsigned* __restrict__ counter,
+                  int k_lo, int k_hi, int area_elems, unsigned* __restrict__ counter,
                   double* __restrict__ partials) {
   extern __shared__ double2 smem_raw[];
   T* smem = reinterpret_cast<T*>(smem_raw);
@@ -211,7 +235,7 @@ lhaf_batch_kernel(const BatchProblem* __restrict__ prob, int count, unsigned tot
     for (uint64_t i = i0; i < i1; ++i) {
       const uint64_t z = i ^ (i >> 1);
       const int k = __popcll(z);
-      if (k == 0) continue;
+      if (k == 0 || k < k_lo || k > k_hi) continue;
       Term t = subset_term_full<T>(P, z, k, area, lane);
       if ((P.n - k) & 1) t = Term{-t.re_hi, -t.re_lo, -t.im_hi, -t.im_lo};
       acc.add(t);
@@ -223,9 +247,14 @@ lhaf_batch_kernel(const BatchProblem* __restrict__ prob, int count, unsigned tot
   }
 }
 
-// One thread per problem: its chunk partials in increasing order. out[p] = (re, im, sum|p|).
+// One thread per problem: its chunk partials in increasing chunk order, the class-0 partial
+// of a chunk before its class-1 partial (nclass = 1 or 2 popcount classes, partials of class
+// c at partials + c * total_chunks * 5). A class that holds no subset of a chunk wrote an
+// exact zero there, so a problem's result does not depend on whether the second class ran.
+// out[p] = (re, im, sum|p|).
 __global__ void lhaf_batch_finalize_kernel(const BatchProblem* __restrict__ prob, int count,
                                            const double* __restrict__ partials,
+                                           unsigned total_chunks, int nclass,
                                            double* __restrict__ out) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= count) return;
@@ -233,11 +262,13 @@ __global__ void lhaf_batch_finalize_kernel(const BatchProblem* __restrict__ prob
   DDAcc a;
   a.zero();
   for (unsigned c = 0; c < Q.nchunks; ++c) {
-    const double* q = partials + (size_t)(Q.chunk_base + c) * 5;
-    double s, e;
-    DDAcc::two_sum(a.re_hi, q[0], s, e); a.re_hi = s; a.re_lo += e + q[1];
-    DDAcc::two_sum(a.im_hi, q[2], s, e); a.im_hi = s; a.im_lo += e + q[3];
-    a.abs_sum += q[4];
+    for (int cls = 0; cls < nclass; ++cls) {
+      const double* q = partials + ((size_t)cls * total_chunks + Q.chunk_base + c) * 5;
+      double s, e;
+      DDAcc::two_sum(a.re_hi, q[0], s, e); a.re_hi = s; a.re_lo += e + q[1];
+      DDAcc::two_sum(a.im_hi, q[2], s, e); a.im_hi = s; a.im_lo += e + q[3];
+      a.abs_sum += q[4];
+    }
   }
   out[3 * p + 0] = Q.n == 0 ? 1.0 : a.re_hi + a.re_lo;
   out[3 * p + 1] = Q.n == 0 ? 0.0 : a.im_hi + a.im_lo;
@@ -366,6 +397,7 @@ bool make_plan(int N, const DeviceInfo& dev, int warps_main, int kcap_override, 
   plan.off_v = off; off = align256(off + sizeof(double2) * plan.Ne);
   plan.off_partials = off; off = align256(off + sizeof(double) * 5 * (size_t)plan.nclass * plan.nchunks);
   plan.off_counters = off; off = align256(off + sizeof(unsigned) * kMaxClasses);
+  plan.off_blocks = off; off = align256(off + sizeof(double) * 5 * kReduceBlocks);
   plan.off_out = off; off = align256(off + sizeof(double) * 4);
   plan.bytes = off;
   *p = plan;
@@ -467,9 +499,11 @@ cudaError_t launch_lhaf(const LhafPlan& plan, const double2* base, int ld, const
   e = launch_classes<false>(plan, ws, nullptr, stream);
   if (e != cudaSuccess) return e;
   char* b = static_cast<char*>(ws);
-  lhaf_finalize_kernel<<<1, kFinalizeThreads, 0, stream>>>(
-      reinterpret_cast<const double*>(b + plan.off_partials), plan.nchunks, plan.nclass,
-      reinterpret_cast<double*>(b + plan.off_out));
+  double* blocks = reinterpret_cast<double*>(b + plan.off_blocks);
+  lhaf_partials_kernel<<<kReduceBlocks, kFinalizeThreads, 0, stream>>>(
+      reinterpret_cast<const double*>(b + plan.off_partials), plan.nchunks, plan.nclass, blocks);
+  lhaf_finalize_kernel<<<1, kFinalizeThreads, 0, stream>>>(blocks, kReduceBlocks,
+                                                           reinterpret_cast<double*>(b + plan.off_out));
   return cudaGetLastError();
 }
 
@@ -513,10 +547,47 @@ int batch_warps_for(int n_max, int precision, const DeviceInfo& dev, int warps_p
   return W;
 }
 
+// Blocks per SM of the batch kernel for precision `precision`, W warps and `smem` bytes.
+static int batch_blocks_per_sm(int precision, int W, size_t smem) {
+  int per_sm = 1;
+  if (precision == kPrecC32) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lhaf_batch_kernel<float2>, 32 * W, smem);
+  } else if (precision == kPrecDD) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lhaf_batch_kernel<ddc>, 32 * W, smem);
+  } else {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lhaf_batch_kernel<double2>, 32 * W, smem);
+  }
+  return per_sm < 1 ? 1 : per_sm;
+}
+
+static cudaError_t launch_batch_class(const BatchProblem* d_prob, int count, unsigned total_chunks,
+                                      int k_lo, int k_hi, int area, int W, int precision,
+                                      const DeviceInfo& dev, unsigned* d_counter,
+                                      double* d_partials, cudaStream_t stream) {
+  const int esz = prec_elem_bytes(precision);
+  const size_t smem = (size_t)W * area * esz;
+  unsigned blocks = (unsigned)(batch_blocks_per_sm(precision, W, smem) * dev.sm_count);
+  const unsigned need = (total_chunks + W - 1) / W;
+  if (blocks > need) blocks = need;
+  if (precision == kPrecC32) {
+    lhaf_batch_kernel<float2><<<blocks, 32 * W, smem, stream>>>(
+        d_prob, count, total_chunks, k_lo, k_hi, area, d_counter, d_partials);
+  } else if (precision == kPrecDD) {
+    lhaf_batch_kernel<ddc><<<blocks, 32 * W, smem, stream>>>(
+        d_prob, count, total_chunks, k_lo, k_hi, area, d_counter, d_partials);
+  } else {
+    lhaf_batch_kernel<double2><<<blocks, 32 * W, smem, stream>>>(
+        d_prob, count, total_chunks, k_lo, k_hi, area, d_counter, d_partials);
+  }
+  return cudaGetLastError();
+}
+
+int batch_classes(int n_max) { return n_max > kBatchSplitK ? 2 : 1; }
+
 cudaError_t launch_batch(const BatchInput* d_in, const BatchProblem* d_prob, int count,
                          unsigned total_chunks, int n_max, int precision, int warps,
                          unsigned* d_counter, double* d_partials, double* d_out,
-                         cudaStream_t stream) {
+                         cudaStream_t stream, cudaStream_t side_stream) {
   if (count <= 0) return cudaSuccess;
   DeviceInfo dev;
   cudaError_t e = device_info(&dev);
@@ -524,42 +595,49 @@ cudaError_t launch_batch(const BatchInput* d_in, const BatchProblem* d_prob, int
   expand_batch_kernel<<<count, 256, 0, stream>>>(d_in, d_prob, count);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned), stream);
+  const int nclass = batch_classes(n_max);
+  e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned) * 2, stream);
   if (e != cudaSuccess) return e;
   if (total_chunks > 0) {
     const int esz = prec_elem_bytes(precision);
-    const int area = warp_area_elems(n_max > 0 ? n_max : 1, n_max > 0 ? n_max : 1, esz);
-    const size_t smem = (size_t)warps * area * esz;
-    int per_sm = 1;
-    if (precision == kPrecC32) {
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lhaf_batch_kernel<float2>,
-                                                    32 * warps, smem);
-    } else if (precision == kPrecDD) {
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lhaf_batch_kernel<ddc>,
-                                                    32 * warps, smem);
+    const int nm = n_max > 0 ? n_max : 1;
+    if (nclass == 1) {
+      e = launch_batch_class(d_prob, count, total_chunks, 1, nm, warp_area_elems(nm, nm, esz),
+                             warps, precision, dev, d_counter, d_partials, stream);
     } else {
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lhaf_batch_kernel<double2>,
-                                                    32 * warps, smem);
+      // Class 0 (popcount <= kBatchSplitK, most subsets): small work areas, many warps.
+      const int area0 = warp_area_elems(kBatchSplitK, nm, esz);
+      int W0 = kMaxWarps;
+      while (W0 > 1 && (size_t)W0 * area0 * esz > (size_t)dev.smem_optin) --W0;
+      // Class 1 (larger popcounts) on a side stream, forked from and joined into `stream`.
+      cudaStream_t sc = side_stream;
+      if (!sc) {
+        cudaStream_t* side = nullptr;
+        e = side_streams(&side);
+        if (e != cudaSuccess) return e;
+        sc = side[1];
+      }
+      cudaEvent_t fork = nullptr, join = nullptr;
+      e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventRecord(fork, stream);
+      if (e == cudaSuccess)
+        e = launch_batch_class(d_prob, count, total_chunks, 1, kBatchSplitK, area0, W0,
+                               precision, dev, d_counter, d_partials, stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(sc, fork, 0);
+      if (e == cudaSuccess)
+        e = launch_batch_class(d_prob, count, total_chunks, kBatchSplitK + 1, nm,
+                               warp_area_elems(nm, nm, esz), warps, precision, dev,
+                               d_counter + 1, d_partials + (size_t)total_chunks * 5, sc);
+      if (e == cudaSuccess) e = cudaEventRecord(join, sc);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, join, 0);
+      if (fork) cudaEventDestroy(fork);
+      if (join) cudaEventDestroy(join);
     }
-    if (per_sm < 1) per_sm = 1;
-    unsigned blocks = (unsigned)(per_sm * dev.sm_count);
-    const unsigned need = (total_chunks + warps - 1) / warps;
-    if (blocks > need) blocks = need;
-    if (precision == kPrecC32) {
-      lhaf_batch_kernel<float2><<<blocks, 32 * warps, smem, stream>>>(
-          d_prob, count, total_chunks, area, d_counter, d_partials);
-    } else if (precision == kPrecDD) {
-      lhaf_batch_kernel<ddc><<<blocks, 32 * warps, smem, stream>>>(
-          d_prob, count, total_chunks, area, d_counter, d_partials);
-    } else {
-      lhaf_batch_kernel<double2><<<blocks, 32 * warps, smem, stream>>>(
-          d_prob, count, total_chunks, area, d_counter, d_partials);
-    }
-    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  lhaf_batch_finalize_kernel<<<(count + 127) / 128, 128, 0, stream>>>(d_prob, count, d_partials,
-                                                                      d_out);
+  lhaf_batch_finalize_kernel<<<(count + 127) / 128, 128, 0, stream>>>(
+      d_prob, count, d_partials, total_chunks, total_chunks > 0 ? nclass : 0, d_out);
   return cudaGetLastError();
 }
 

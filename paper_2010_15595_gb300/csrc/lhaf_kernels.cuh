@@ -10,7 +10,8 @@
 namespace gbsh {
 
 constexpr int kMaxWarps = 16;          // warps per CTA of the subset kernel
-constexpr int kFinalizeThreads = 256;  // threads of the finalize kernel
+constexpr int kFinalizeThreads = 256;  // threads of the finalize kernels
+constexpr int kReduceBlocks = 128;     // CTAs of the first level of the final reduction
 constexpr int kMaxClasses = 8;         // popcount classes of one evaluation
 constexpr unsigned kTargetChunks = 1u << 18;  // Gray-code chunks of one evaluation (at most)
 
@@ -28,7 +29,7 @@ struct LhafPlan {
   unsigned nchunks;
   uint64_t chunk_size;
   // workspace layout (byte offsets)
-  size_t off_A0, off_v, off_partials, off_counters, off_out, bytes;
+  size_t off_A0, off_v, off_partials, off_counters, off_blocks, off_out, bytes;
 };
 
 // Device properties cached per device.
@@ -64,11 +65,21 @@ cudaError_t launch_visit_count(const LhafPlan& plan, unsigned* counts, void* ws,
 // Batched evaluation: warps per CTA that fit a problem of n_max pairs (0 if none fit).
 int batch_warps_for(int n_max, int precision, const DeviceInfo& dev, int warps_pref);
 
+// Popcount boundary of the batched evaluation: subsets with popcount <= kBatchSplitK run in
+// one launch with small work areas (many warps per CTA), the rest in a second launch sized
+// for n_max (when n_max > kBatchSplitK). Fixed, so a problem's chunk partials do not depend
+// on the other problems of its batch.
+constexpr int kBatchSplitK = 10;
+int batch_classes(int n_max);
+
 // Expands, evaluates and reduces `count` problems. d_in/d_prob: device tables (problem
 // order = chunk order, largest first); d_out: 3 doubles per problem (re, im, sum |p_Z|).
+// d_counter: 2 counters; d_partials: 2 x total_chunks x 5 doubles. `warps`: warps per CTA of
+// the launch whose work areas are sized for n_max. side_stream: stream of the second class
+// launch (nullptr: the library's side stream).
 cudaError_t launch_batch(const BatchInput* d_in, const BatchProblem* d_prob, int count,
                          unsigned total_chunks, int n_max, int precision, int warps,
                          unsigned* d_counter, double* d_partials, double* d_out,
-                         cudaStream_t stream);
+                         cudaStream_t stream, cudaStream_t side_stream = nullptr);
 
 }  // namespace gbsh

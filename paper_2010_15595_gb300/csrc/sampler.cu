@@ -205,7 +205,7 @@ size_t gbsh_sampler::chain_mem_estimate(int nphot) const {
     if (N > cfg.n_cap) break;
     const int Ne = N + (N & 1), n = Ne / 2;
     const size_t chunks = n > 0 ? ((size_t)1 << n) / gbsh::batch_chunk_size(n) : 0;
-    total += sizeof(double2) * ((size_t)Ne * Ne + Ne) + 40 * chunks + 128 + 4 * (size_t)N;
+    total += sizeof(double2) * ((size_t)Ne * Ne + Ne) + 2 * 40 * chunks + 128 + 4 * (size_t)N;
   }
   return total;
 }

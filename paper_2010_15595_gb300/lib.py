@@ -63,6 +63,8 @@ def load() -> ctypes.CDLL:
         "gbsh_lhaf_batch": ([vp, vp, vp, i, vp, vp, i, vp], i),
         "gbsh_gbs_prob_batch": ([vp, i, i, vp, ctypes.c_int64, vp, i, vp, vp, vp, i, vp], i),
         "gbsh_set_batch_tuning": ([i, i, i], i),
+        "gbsh_set_batch_graphs": ([i], i),
+        "gbsh_batch_graph_stats": ([ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -76,7 +78,8 @@ def exported_symbols():
     return ["gbsh_strerror", "gbsh_version", "gbsh_lhaf", "gbsh_lhaf_workspace_size",
             "gbsh_lhaf_async", "gbsh_gbs_prob", "gbsh_subset_terms", "gbsh_visit_counts",
             "gbsh_set_lhaf_tuning", "gbsh_lhaf_plan", "gbsh_lhaf_noalloc", "gbsh_lhaf_batch",
-            "gbsh_gbs_prob_batch", "gbsh_set_batch_tuning"]
+            "gbsh_gbs_prob_batch", "gbsh_set_batch_tuning", "gbsh_set_batch_graphs",
+            "gbsh_batch_graph_stats"]
 
 
 def _strerror(code: int) -> str:
@@ -284,3 +287,15 @@ def gbs_prob_batch(B, gammas, patterns, p_vacs=None, precision=PREC_FP64, stream
 
 def set_batch_tuning(precision: int, n_max: int, warps_per_cta: int):
     _check(load().gbsh_set_batch_tuning(precision, n_max, warps_per_cta), "gbsh_set_batch_tuning")
+
+
+def set_batch_graphs(enable: bool):
+    """CUDA-graph replay of repeated batched launch shapes (on by default)."""
+    _check(load().gbsh_set_batch_graphs(1 if enable else 0), "gbsh_set_batch_graphs")
+
+
+def batch_graph_stats() -> dict:
+    """{"captures": graphs captured, "replays": graph launches} of the batched path so far."""
+    c, r = ctypes.c_longlong(), ctypes.c_longlong()
+    _check(load().gbsh_batch_graph_stats(ctypes.byref(c), ctypes.byref(r)), "gbsh_batch_graph_stats")
+    return {"captures": c.value, "replays": r.value}

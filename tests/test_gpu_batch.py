@@ -122,6 +122,50 @@ def test_c32_finite_at_batched_workload_sizes(gbsh):
     assert np.all(np.isfinite(c32.real)) and np.all(np.isfinite(c32.imag))
 
 
+def test_batch_graph_replay_bit_identical(gbsh):
+    """A repeated launch shape is captured into a CUDA graph on its second use and replayed
+    afterwards; replays give the direct launch's bits, also for new values of the same shape
+    (the per-call tables are uploaded before each launch)."""
+    rng = np.random.default_rng(21)
+    sizes = [12, 26, 8, 22, 30, 16]
+    mats_a = [W.random_complex_symmetric(N, rng) for N in sizes]
+    mats_b = [W.random_complex_symmetric(N, rng) for N in sizes]
+    try:
+        gbsh.set_batch_graphs(False)
+        direct_a = gbsh.lhaf_batch(mats_a)
+        direct_b = gbsh.lhaf_batch(mats_b)
+        gbsh.set_batch_graphs(True)
+        s0 = gbsh.batch_graph_stats()
+        runs = [gbsh.lhaf_batch(m) for m in (mats_a, mats_a, mats_b, mats_a)]
+        s1 = gbsh.batch_graph_stats()
+    finally:
+        gbsh.set_batch_graphs(True)
+    assert s1["captures"] >= s0["captures"] + 1
+    assert s1["replays"] >= s0["replays"] + 3
+    assert np.array_equal(runs[0], direct_a) and np.array_equal(runs[1], direct_a)
+    assert np.array_equal(runs[2], direct_b) and np.array_equal(runs[3], direct_a)
+
+
+def test_batch_graph_same_count_other_layout(gbsh):
+    """Two batches with equal count, largest size and chunk total but another size mix (so
+    other workspace offsets) must not share a graph: alternating them keeps direct results."""
+    rng = np.random.default_rng(22)
+    # chunk totals: 2^n / chunk(n) summed; {14, 14, 6, 6} and {14, 14, 4, 8} differ in the
+    # small problems' sizes, which moves the expanded-matrix area and everything after it
+    sizes_a, sizes_b = [14, 14, 6, 6], [14, 14, 4, 8]
+    mats_a = [W.random_complex_symmetric(N, rng) for N in sizes_a]
+    mats_b = [W.random_complex_symmetric(N, rng) for N in sizes_b]
+    try:
+        gbsh.set_batch_graphs(False)
+        da, db = gbsh.lhaf_batch(mats_a), gbsh.lhaf_batch(mats_b)
+        gbsh.set_batch_graphs(True)
+        runs = [gbsh.lhaf_batch(m) for m in (mats_a, mats_b, mats_a, mats_b, mats_a, mats_b)]
+    finally:
+        gbsh.set_batch_graphs(True)
+    for i, r in enumerate(runs):
+        assert np.array_equal(r, da if i % 2 == 0 else db), i
+
+
 def test_batch_rejects_bad_input(gbsh):
     with pytest.raises(gbsh.GbshError):
         gbsh.lhaf_batch([np.ones((61, 61), complex)])
