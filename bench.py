@@ -140,8 +140,9 @@ def kernel_source_hash() -> str:
 
 
 def recorded_traffic(N: int):
-    """DRAM bytes per launch of the subset kernel from the committed ncu summary, if it was
-    taken on the current kernel sources; else None."""
+    """DRAM bytes of one evaluation (every launch of gbsh_lhaf: expansion, the popcount-class
+    launches of the subset kernel, the two finalize levels) from the committed ncu summary, if
+    it was taken on the current kernel sources; else None."""
     path = os.path.join(ROOT, "profiles", "lhaf_subsets_dram_traffic.json")
     try:
         with open(path) as f:
@@ -150,7 +151,7 @@ def recorded_traffic(N: int):
         return None
     if rec.get("kernel_source_hash") != kernel_source_hash():
         return None
-    return rec.get("bytes_per_launch", {}).get(str(N))
+    return rec.get("bytes_per_evaluation", {}).get(str(N))
 
 
 # ------------------------------------------------------------------ CPU oracle timing
