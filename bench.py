@@ -130,10 +130,15 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ traffic record
 
+# Sources that define the subset kernel, its launches and its finalize (the sampler and the
+# C-ABI wrappers do not change what one evaluation moves through DRAM).
+KERNEL_SOURCES = ("lhaf_core.cuh", "lhaf_kernels.cu", "lhaf_kernels.cuh", "lhaf_types.cuh")
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2010_15595_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in KERNEL_SOURCES:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -240,28 +245,65 @@ def run_ours(args, rank, world, local_rank):
            "h2d_bytes_per_step": int(A.nbytes), "d2h_bytes_per_step": 24,
            "api": "gbsh_lhaf (host matrix in, host result out)"}
 
-    n50 = None
-    if args.n50 and rank == 0:
-        A50 = workloads.large_lhaf(50)
-        d50 = torch.from_numpy(A50).to(dev)
-        ws50 = torch.empty(lib.workspace_size(50), dtype=torch.uint8, device=dev)
-        o50 = torch.empty(1, dtype=torch.complex128, device=dev)
-        lib.lhaf_async(d50, o50, ws50, stream=stream)
+    def large_eval(N, warm):
+        """One timed evaluation of the large single loop hafnian of size N (after a warm-up
+        evaluation if `warm`), CUDA events on the launching stream."""
+        AL = workloads.large_lhaf(N)
+        dL = torch.from_numpy(AL).to(dev)
+        wsL = torch.empty(lib.workspace_size(N), dtype=torch.uint8, device=dev)
+        oL = torch.empty(1, dtype=torch.complex128, device=dev)
+        if warm:
+            lib.lhaf_async(dL, oL, wsL, stream=stream)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         flush.zero_()
         e0.record(stream)
-        lib.lhaf_async(d50, o50, ws50, stream=stream)
+        lib.lhaf_async(dL, oL, wsL, stream=stream)
         e1.record(stream)
         torch.cuda.synchronize()
-        s50 = e0.elapsed_time(e1) / 1e3
-        ach50 = workmodel.lhaf_flops(50) / s50 / 1e12
-        n50 = {"workload": "single loop hafnian N=50 (M=50 Haar U, r=0.8, gamma~CN(0,0.1^2)), "
-                           "2^25 subsets, 1 warm-up + 1 timed evaluation",
-               "seconds": s50, "value": workmodel.subset_count(50) / s50, "unit": UNIT,
-               "roofline": {"bound": "alu", "achieved": ach50, "peak": peak,
-                            "unit": "TFLOP/s", "frac": ach50 / peak},
-               "plan": lib.plan(50)}
+        sec = e0.elapsed_time(e1) / 1e3
+        ach = workmodel.lhaf_flops(N) / sec / 1e12
+        return {"workload": f"single loop hafnian N={N} (M={N} Haar U, r=0.8, gamma~CN(0,0.1^2)), "
+                            f"2^{N // 2} subsets, {'1 warm-up + ' if warm else ''}1 timed evaluation",
+                "seconds": sec, "value": workmodel.subset_count(N) / sec, "unit": UNIT,
+                "roofline": {"bound": "alu", "achieved": ach, "peak": peak,
+                             "unit": "TFLOP/s", "frac": ach / peak},
+                "plan": lib.plan(N), "lhaf": [complex(oL.item()).real, complex(oL.item()).imag]}
+
+    n50 = large_eval(50, True) if (args.n50 and rank == 0) else None
+    n56 = large_eval(56, False) if (args.n56 and rank == 0) else None
+
+    def small_latency(A, name, calls=200):
+        """Per-call cost of a small evaluation: host wall time of a synchronous gbsh_lhaf with a
+        host matrix (copies in and out included), median of `calls`; and device time per
+        evaluation of `calls` back-to-back gbsh_lhaf_async on device buffers (CUDA events)."""
+        N = A.shape[0]
+        for _ in range(5):
+            lib.lhaf(A)
+        walls = []
+        for _ in range(calls):
+            t0 = time.perf_counter()
+            lib.lhaf(A)
+            walls.append(time.perf_counter() - t0)
+        dA = torch.from_numpy(A).to(dev)
+        wsS = torch.empty(lib.workspace_size(N), dtype=torch.uint8, device=dev)
+        oS = torch.empty(1, dtype=torch.complex128, device=dev)
+        lib.lhaf_async(dA, oS, wsS, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(calls):
+            lib.lhaf_async(dA, oS, wsS, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return {"workload": name, "sync_call_us_median": 1e6 * statistics.median(walls),
+                "device_us_per_eval": 1e3 * e0.elapsed_time(e1) / calls,
+                "kernels_per_eval": lib.plan(N)["kernels"]}
+
+    small = None
+    if args.small and rank == 0:
+        small = [small_latency(workloads.single_lhaf_n16(), "N=16 (M=16 Haar U, r=0.6, gamma~CN(0,0.3^2)), 256 subsets"),
+                 small_latency(workloads.single_lhaf_mid(32), "N=32 (M=32 Haar U, r~U[0.4,0.9], gamma~CN(0,0.2^2)), 65536 subsets", calls=50)]
 
     batch = None
     if args.batch and rank == 0:
@@ -300,6 +342,8 @@ def run_ours(args, rank, world, local_rank):
             "result": {"lhaf": [lhaf_val.real, lhaf_val.imag], "kappa": kappa,
                        "err_est": kappa * 2.0 ** -53},
             "n50": n50,
+            **({"n56": n56} if n56 is not None else {}),
+            "small": small,
             "batch": batch,
             "serving": serving,
             "paper_context": "Fig. 3: N=40 in 44.9 s (23.3k subset-terms/s), N=50 in 2499 s "
@@ -351,7 +395,8 @@ def run_batch_workload(lib, workloads, workmodel, dev, stream, count=4096):
 def run_serving_workload(args):
     """Chain-rule sampler (Sec. III) on the serving state: M=100 modes, Haar U, r=0.8 on 25
     input modes (mean ~20 photons), output displacement ~CN(0, 0.1^2), Fock cutoff 4, loop
-    hafnians up to N=36. Plain path (one launch per loop hafnian, one sample at a time) vs
+    hafnians up to N=36. Plain path (one single-evaluation launch sequence and one
+    synchronisation per loop hafnian, one sample at a time) vs
     the served path (continuous batching); Poisson arrivals at fixed multiples of the plain
     throughput; latencies from submission to completion."""
     import numpy as np
@@ -522,6 +567,9 @@ def main(argv=None):
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--n", type=int, default=40)
     p.add_argument("--no-n50", dest="n50", action="store_false")
+    p.add_argument("--no-small", dest="small", action="store_false")
+    p.add_argument("--n56", action="store_true",
+                   help="also time one N=56 evaluation (2^28 subsets, about a minute)")
     p.add_argument("--no-batch", dest="batch", action="store_false")
     p.add_argument("--no-serving", dest="serving", action="store_false")
     p.add_argument("--serve-plain", type=int, default=6)

@@ -248,7 +248,9 @@ typedef struct {
   int max_active;           /* samples in flight (device slots); 1 with batching = 0 */
   size_t mem_budget;        /* device bytes admitted samples may use (admission control) */
   int batching;             /* 1: continuous batching, one launch per tick for all samples;
-                               0: plain path, one launch per loop hafnian, one sample at a time */
+                               0: plain path, one single-evaluation launch sequence and one
+                                  synchronisation per loop hafnian (a one-problem batch for
+                                  GBSH_PREC_C32), one sample at a time */
   int precision;            /* GBSH_PREC_FP64 or GBSH_PREC_C32 */
   int device;               /* CUDA device the sampler's worker thread uses */
   int threshold;            /* 1: report threshold-detector clicks (s_i > 0 -> 1), the

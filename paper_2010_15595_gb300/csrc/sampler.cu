@@ -292,13 +292,42 @@ int gbsh_sampler::tick(std::vector<Chain>& active) {
     e = gbsh::batch_run(L, in, nc, cfg.precision, 0, ws, st, out3.data());
     if (e != cudaSuccess) return from_cuda(e);
   } else {
-    // plain path: one launch sequence (and one synchronisation) per loop hafnian
+    // plain path: one single-evaluation launch sequence (expansion of B, the fill vector and
+    // the pattern on the device, the popcount-class launches, finalize) and one
+    // synchronisation per loop hafnian -- what a caller of gbsh_gbs_prob would do per
+    // candidate. The complex-FP32 and double-double variants exist only in the batched
+    // kernel, so for them each candidate is a one-problem batch instead.
+    gbsh::DeviceInfo dev;
+    e = gbsh::device_info(&dev);
+    if (e != cudaSuccess) return from_cuda(e);
+    e = gbsh::ensure_constants();
+    if (e != cudaSuccess) return from_cuda(e);
     for (int q = 0; q < nc; ++q) {
-      gbsh::BatchLayout L = gbsh::batch_layout(&Ns[q], 1, 0);
-      rc = ensure_ws(L.bytes);
+      if (Ns[q] == 0) {
+        out3[3 * (size_t)q] = 1.0;
+        out3[3 * (size_t)q + 1] = 0.0;
+        out3[3 * (size_t)q + 2] = 1.0;
+        continue;
+      }
+      if (cfg.precision != GBSH_PREC_FP64) {
+        gbsh::BatchLayout L = gbsh::batch_layout(&Ns[q], 1, 0);
+        rc = ensure_ws(L.bytes);
+        if (rc != GBSH_OK) return rc;
+        std::vector<gbsh::BatchInput> one(1, in[q]);
+        e = gbsh::batch_run(L, one, 1, cfg.precision, 0, ws, st, &out3[3 * (size_t)q]);
+        if (e != cudaSuccess) return from_cuda(e);
+        continue;
+      }
+      gbsh::LhafPlan plan;
+      if (!gbsh::make_plan(Ns[q], dev, 0, 0, &plan)) return GBSH_EINVAL;
+      rc = ensure_ws(plan.bytes);
       if (rc != GBSH_OK) return rc;
-      std::vector<gbsh::BatchInput> one(1, in[q]);
-      e = gbsh::batch_run(L, one, 1, cfg.precision, 0, ws, st, &out3[3 * (size_t)q]);
+      const gbsh::BatchInput& b = in[q];
+      e = gbsh::launch_lhaf(plan, b.base, b.ld, b.diag, b.idx, ws, st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&out3[3 * (size_t)q], static_cast<char*>(ws) + plan.off_out,
+                            3 * sizeof(double), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
       if (e != cudaSuccess) return from_cuda(e);
     }
   }
