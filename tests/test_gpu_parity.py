@@ -234,6 +234,39 @@ def test_visit_each_subset_once(gbsh, N):
     assert (c[1:] == 1).all()
 
 
+def test_visit_each_subset_once_default_ladder(gbsh):
+    """N = 40 with the default launch plan (three popcount classes on the warps-per-CTA
+    ladder, 2^18 chunks, classes overlapped on side streams): every nonempty subset once."""
+    assert gbsh.plan(40)["nclass"] >= 3
+    c = gbsh.visit_counts(40).cpu().numpy()
+    assert c[0] == 0
+    assert (c[1:] == 1).all()
+
+
+def test_async_on_user_stream_is_ordered(gbsh):
+    """gbsh_lhaf_async on a non-default stream: the popcount classes that run on the
+    library's side streams are joined back into the caller's stream, so work queued on that
+    stream after the call sees the finished result (the output is cleared before each call)."""
+    import torch
+    A = W.single_lhaf_mid(34)
+    assert gbsh.plan(34)["nclass"] >= 2
+    ref = gbsh.lhaf(A)
+    s = torch.cuda.Stream()
+    dA = torch.from_numpy(A).cuda()
+    ws = torch.empty(gbsh.workspace_size(34), dtype=torch.uint8, device="cuda")
+    out = torch.zeros(1, dtype=torch.complex128, device="cuda")
+    copies = []
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        for _ in range(3):
+            out.zero_()
+            gbsh.lhaf_async(dA, out, ws, stream=s)
+            copies.append(out.clone())
+    s.synchronize()
+    for c in copies:
+        assert complex(c.item()) == ref
+
+
 def test_subset_terms_match_oracle(gbsh):
     """Individual terms p_Z at N=40 for a seeded sample of subsets of every popcount."""
     import torch
