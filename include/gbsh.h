@@ -88,6 +88,12 @@ size_t gbsh_lhaf_workspace_size(int N);
  *   workspace   device buffer of at least gbsh_lhaf_workspace_size(N) bytes, 256-byte
  *               aligned, owned by the caller; must not be used by another call that may
  *               run at the same time.
+ * Streams: the popcount classes after the first run on side streams that the library
+ * creates once per device; they are forked from `stream` and joined back into it with
+ * events, so the whole evaluation is ordered after the work already queued on `stream` and
+ * before the work queued on it afterwards, as if it ran on `stream` alone. Concurrent calls
+ * from several threads share the side streams (correct, possibly serialised). The first
+ * multi-class evaluation on a device creates them; make it before any stream capture.
  * N == 0 writes 1 to d_out. Errors: GBSH_EINVAL, GBSH_ECUDA (launch errors only; device
  * faults surface at the caller's next synchronisation).
  */
