@@ -88,13 +88,22 @@ cudaGraphExec_t graph_capture(const GraphKey& key, const BatchLayout& L, char* w
   {
     std::lock_guard<std::mutex> lk(g_graph_mu);
     if (!g_cap_stream[key.dev]) {
-      if (cudaStreamCreateWithFlags(&g_cap_stream[key.dev], cudaStreamNonBlocking) != cudaSuccess ||
-          cudaStreamCreateWithFlags(&g_cap_side[key.dev], cudaStreamNonBlocking) != cudaSuccess)
+      cudaStream_t a = nullptr, b = nullptr;
+      if (cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking) != cudaSuccess) {
+        if (a) cudaStreamDestroy(a);
+        cudaGetLastError();
         return nullptr;
+      }
+      g_cap_side[key.dev] = b;
+      g_cap_stream[key.dev] = a;
     }
   }
   cudaStream_t cs = g_cap_stream[key.dev];
-  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return nullptr;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();  // e.g. another thread is capturing on this stream: launch directly
+    return nullptr;
+  }
   cudaError_t e = launch_batch(reinterpret_cast<const BatchInput*>(w + L.off_in),
                                reinterpret_cast<const BatchProblem*>(w + L.off_prob), count,
                                L.total_chunks, L.n_max, precision, W,

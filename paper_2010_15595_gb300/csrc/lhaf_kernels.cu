@@ -441,7 +441,10 @@ static cudaError_t side_streams(cudaStream_t** out) {
   if (!made[dev]) {
     for (int c = 1; c < kMaxClasses; ++c) {
       e = cudaStreamCreateWithFlags(&streams[dev][c], cudaStreamNonBlocking);
-      if (e != cudaSuccess) return e;
+      if (e != cudaSuccess) {
+        for (int d = 1; d < c; ++d) cudaStreamDestroy(streams[dev][d]);
+        return e;
+      }
     }
     made[dev] = true;
   }
