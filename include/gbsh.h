@@ -79,6 +79,8 @@ int gbsh_lhaf(const gbsh_c128* A, int N, int lda, gbsh_c128* out, double* err_es
 
 /* Bytes of device workspace gbsh_lhaf_async needs for size N (0 for N outside 1..MAX_N). */
 size_t gbsh_lhaf_workspace_size(int N);
+/* The same for gbsh_lhaf_async_ex in `precision` (0 for an unsupported precision). */
+size_t gbsh_lhaf_workspace_size_ex(int N, int precision);
 
 /*
  * gbsh_lhaf_async — gbsh_lhaf with everything on the device and no synchronisation.
@@ -100,6 +102,21 @@ size_t gbsh_lhaf_workspace_size(int N);
 int gbsh_lhaf_async(const gbsh_c128* dA, int N, int lda, gbsh_c128* d_out, double* d_abs_sum,
                     void* workspace, size_t workspace_bytes, void* stream);
 
+/*
+ * gbsh_lhaf_ex, gbsh_lhaf_async_ex — gbsh_lhaf and gbsh_lhaf_async with the per-subset
+ * arithmetic chosen by `precision`: GBSH_PREC_FP64 (what gbsh_lhaf and gbsh_lhaf_async
+ * use) or GBSH_PREC_TF (triple-float, the accurate path; see GBSH_PREC_TF below). Every
+ * other argument, the stream semantics and the errors are those of the plain entry points;
+ * any other precision is GBSH_EINVAL. err_est uses the precision's unit roundoff (2^-53
+ * for FP64, 2^-70 for triple-float). For gbsh_lhaf_async_ex the workspace must hold
+ * gbsh_lhaf_workspace_size_ex(N, precision) bytes.
+ */
+int gbsh_lhaf_ex(const gbsh_c128* A, int N, int lda, int precision, gbsh_c128* out,
+                 double* err_est, void* stream);
+int gbsh_lhaf_async_ex(const gbsh_c128* dA, int N, int lda, int precision, gbsh_c128* d_out,
+                       double* d_abs_sum, void* workspace, size_t workspace_bytes,
+                       void* stream);
+
 /* Per-subset arithmetic of the batched entry points. GBSH_PREC_FP64: complex FP64
  * throughout. GBSH_PREC_C32: each subset term in complex FP32 (the characteristic
  * polynomial, traces and exp-polynomial steps), the signed sum over subsets still
@@ -116,6 +133,19 @@ int gbsh_lhaf_async(const gbsh_c128* dA, int N, int lda, gbsh_c128* d_out, doubl
  * cancellation of the signed subset sum) is too coarse; the cross-subset sum is the same
  * compensated FP64 sum. */
 #define GBSH_PREC_DD 3
+/* GBSH_PREC_TF: each subset term in triple-float arithmetic -- every real number the
+ * Hessenberg reduction, La Budde's recursion and the power series handle is the unevaluated
+ * sum of three FP32 words (~72-bit significand), and each term reaches the compensated
+ * cross-subset sum as an exact double-double. This is the path that meets the relative
+ * tolerance the heavy cancellation of the signed subset sum demands at N >= 32 (the
+ * accuracy concern of Sec. IV and Fig. 2): FP64 per subset leaves the N = 40 and N = 50
+ * configuration matrices about 6e-8 and 1.5e-5 off, triple-float about 1e-13 and 1e-10 in
+ * a CPU emulation of the same arithmetic. It runs on the FP32 pipe, which GB300 issues at
+ * 64 times its FP64 rate. Accepted by the batched entry points and by the _ex
+ * single-evaluation entry points below. Its words are FP32, so entries of the matrix, the
+ * Hessenberg form and the polynomial coefficients must stay within about 2^-78 .. 2^127
+ * in magnitude for full precision (every workload of the paper does by a wide margin). */
+#define GBSH_PREC_TF 4
 
 /*
  * gbsh_lhaf_batch — loop hafnians of `count` matrices of uneven size in one persistent
@@ -197,6 +227,10 @@ int gbsh_gbs_prob(const gbsh_c128* B, int M, int ldb, const gbsh_c128* gamma,
  */
 int gbsh_subset_terms(const gbsh_c128* dA, int N, int lda, const uint64_t* d_z, int count,
                       gbsh_c128* d_out, void* stream);
+/* The same with the per-subset arithmetic of `precision` (GBSH_PREC_FP64 or GBSH_PREC_TF);
+ * triple-float terms are rounded to the nearest complex double on output. */
+int gbsh_subset_terms_ex(const gbsh_c128* dA, int N, int lda, int precision, const uint64_t* d_z,
+                         int count, gbsh_c128* d_out, void* stream);
 
 /*
  * gbsh_visit_counts — diagnostic: runs the subset enumeration of gbsh_lhaf for size N
@@ -225,6 +259,9 @@ int gbsh_set_lhaf_tuning(int warps_per_cta, int kcap);
  * Errors: GBSH_EINVAL for N outside 1..GBSH_MAX_N, GBSH_ECUDA without a device.
  */
 int gbsh_lhaf_plan(int N, int* nclass, int* kernels, int* warps, int* kcap, int* nchunks);
+/* The same for the plan of `precision` (GBSH_PREC_FP64 or GBSH_PREC_TF). */
+int gbsh_lhaf_plan_ex(int N, int precision, int* nclass, int* kernels, int* warps, int* kcap,
+                      int* nchunks);
 
 /* ---------------------------------------------------------------- chain-rule sampler
  * The sampling algorithm of Sec. III (steps 2-6) for a pure Gaussian state, served with
@@ -331,6 +368,11 @@ int gbsh_philox4x32(const uint32_t counter[4], const uint32_t key[2], uint32_t o
 #define GBSH_NOALLOC_SCRATCH_BYTES (8u << 20)
 int gbsh_lhaf_noalloc(const gbsh_c128* dA, int N, int lda, gbsh_c128* d_out, double* d_abs_sum,
                       void* stream);
+/* Diagnostic: the number of subset chunks gbsh_lhaf_noalloc would use for size N on the
+ * current device (the default plan's count, or fewer where that plan's scratch would not
+ * fit the fixed array), or GBSH_ENOMEM when no chunking fits. Runs no kernel and touches
+ * no device memory. Errors: GBSH_EINVAL for N outside 1..GBSH_MAX_N, GBSH_ECUDA. */
+int gbsh_lhaf_noalloc_plan(int N, int* nchunks);
 
 #ifdef __cplusplus
 }

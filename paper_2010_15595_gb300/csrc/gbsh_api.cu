@@ -74,7 +74,11 @@ bool is_device_pointer(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-int plan_for(int N, gbsh::LhafPlan* plan) {
+// Precisions of the single-evaluation entry points.
+bool valid_single_precision(int p) { return p == GBSH_PREC_FP64 || p == GBSH_PREC_TF; }
+
+int plan_for(int N, gbsh::LhafPlan* plan, int prec = GBSH_PREC_FP64) {
+  if (!valid_single_precision(prec)) return GBSH_EINVAL;
   gbsh::DeviceInfo dev;
   GBSH_CUDA(gbsh::device_info(&dev));
   GBSH_CUDA(gbsh::ensure_constants());
@@ -84,8 +88,19 @@ int plan_for(int N, gbsh::LhafPlan* plan) {
     w = g_tune_warps;
     k = g_tune_kcap;
   }
-  if (!gbsh::make_plan(N, dev, w, k, plan)) return GBSH_EINVAL;
+  const int kprec = prec == GBSH_PREC_TF ? gbsh::kPrecTF : gbsh::kPrecFP64;
+  if (!gbsh::make_plan(N, dev, w, k, plan, gbsh::kTargetChunks, kprec)) return GBSH_EINVAL;
   return GBSH_OK;
+}
+
+// Unit roundoff of a precision's per-subset arithmetic (for the error estimate).
+double unit_roundoff(int prec) {
+  switch (prec) {
+    case GBSH_PREC_C32: return std::ldexp(1.0, -24);
+    case GBSH_PREC_DD: return std::ldexp(1.0, -100);
+    case GBSH_PREC_TF: return std::ldexp(1.0, -70);
+    default: return std::ldexp(1.0, -53);
+  }
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -105,15 +120,15 @@ int run_sync(const gbsh::LhafPlan& plan, const double2* base, int ld, const doub
   return GBSH_OK;
 }
 
-double err_from(double abs_sum, gbsh_c128 v) {
+double err_from(double abs_sum, gbsh_c128 v, int prec = GBSH_PREC_FP64) {
   double mag = std::hypot(v.re, v.im);
   if (mag == 0.0) return INFINITY;
-  return std::ldexp(1.0, -53) * abs_sum / mag;
+  return unit_roundoff(prec) * abs_sum / mag;
 }
 
 
 // ---------------------------------------------------------------- batched evaluation
-int g_batch_warps[4][gbsh::kMaxN / 2 + 1] = {};  // per precision and n_max; 0 = default
+int g_batch_warps[gbsh::kNumPrec][gbsh::kMaxN / 2 + 1] = {};  // per precision and n_max; 0 = default
 using gbsh::BatchLayout;
 using gbsh::batch_layout;
 
@@ -131,7 +146,8 @@ int batch_run(BatchLayout& L, const std::vector<gbsh::BatchInput>& in, int count
 }
 
 bool valid_precision(int p) {
-  return p == GBSH_PREC_FP64 || p == GBSH_PREC_C32 || p == GBSH_PREC_MIXED || p == GBSH_PREC_DD;
+  return p == GBSH_PREC_FP64 || p == GBSH_PREC_C32 || p == GBSH_PREC_MIXED || p == GBSH_PREC_DD ||
+         p == GBSH_PREC_TF;
 }
 
 
@@ -201,9 +217,14 @@ int gbsh_set_lhaf_tuning(int warps_per_cta, int kcap) {
 }
 
 int gbsh_lhaf_plan(int N, int* nclass, int* kernels, int* warps, int* kcap, int* nchunks) {
+  return gbsh_lhaf_plan_ex(N, GBSH_PREC_FP64, nclass, kernels, warps, kcap, nchunks);
+}
+
+int gbsh_lhaf_plan_ex(int N, int precision, int* nclass, int* kernels, int* warps, int* kcap,
+                      int* nchunks) {
   if (N < 1 || N > GBSH_MAX_N) return GBSH_EINVAL;
   gbsh::LhafPlan plan;
-  int rc = plan_for(N, &plan);
+  int rc = plan_for(N, &plan, precision);
   if (rc != GBSH_OK) return rc;
   if (nclass) *nclass = plan.nclass;
   if (kernels) *kernels = plan.nclass + 3;
@@ -213,16 +234,23 @@ int gbsh_lhaf_plan(int N, int* nclass, int* kernels, int* warps, int* kcap, int*
   return GBSH_OK;
 }
 
-size_t gbsh_lhaf_workspace_size(int N) {
+size_t gbsh_lhaf_workspace_size(int N) { return gbsh_lhaf_workspace_size_ex(N, GBSH_PREC_FP64); }
+
+size_t gbsh_lhaf_workspace_size_ex(int N, int precision) {
   if (N < 1 || N > GBSH_MAX_N) return 0;
   gbsh::LhafPlan plan;
-  if (plan_for(N, &plan) != GBSH_OK) return 0;
+  if (plan_for(N, &plan, precision) != GBSH_OK) return 0;
   return plan.bytes;
 }
 
 int gbsh_lhaf(const gbsh_c128* A, int N, int lda, gbsh_c128* out, double* err_est,
               void* stream) {
-  if (!out || N < 0 || N > GBSH_MAX_N) return GBSH_EINVAL;
+  return gbsh_lhaf_ex(A, N, lda, GBSH_PREC_FP64, out, err_est, stream);
+}
+
+int gbsh_lhaf_ex(const gbsh_c128* A, int N, int lda, int precision, gbsh_c128* out,
+                 double* err_est, void* stream) {
+  if (!out || N < 0 || N > GBSH_MAX_N || !valid_single_precision(precision)) return GBSH_EINVAL;
   if (N == 0) {
     out->re = 1.0;
     out->im = 0.0;
@@ -232,7 +260,7 @@ int gbsh_lhaf(const gbsh_c128* A, int N, int lda, gbsh_c128* out, double* err_es
   if (!A || lda < N) return GBSH_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   gbsh::LhafPlan plan;
-  int rc = plan_for(N, &plan);
+  int rc = plan_for(N, &plan, precision);
   if (rc != GBSH_OK) return rc;
   int dev = 0;
   GBSH_CUDA(cudaGetDevice(&dev));
@@ -256,24 +284,29 @@ int gbsh_lhaf(const gbsh_c128* A, int N, int lda, gbsh_c128* out, double* err_es
   double asum = 0.0;
   rc = run_sync(plan, base, ld, nullptr, nullptr, ws, st, out, &asum);
   if (rc != GBSH_OK) return rc;
-  if (err_est) *err_est = err_from(asum, *out);
+  if (err_est) *err_est = err_from(asum, *out, precision);
   return GBSH_OK;
 }
 
 int gbsh_lhaf_async(const gbsh_c128* dA, int N, int lda, gbsh_c128* d_out, double* d_abs_sum,
                     void* workspace, size_t workspace_bytes, void* stream) {
-  if (!d_out || N < 0 || N > GBSH_MAX_N) return GBSH_EINVAL;
+  return gbsh_lhaf_async_ex(dA, N, lda, GBSH_PREC_FP64, d_out, d_abs_sum, workspace,
+                            workspace_bytes, stream);
+}
+
+int gbsh_lhaf_async_ex(const gbsh_c128* dA, int N, int lda, int precision, gbsh_c128* d_out,
+                       double* d_abs_sum, void* workspace, size_t workspace_bytes,
+                       void* stream) {
+  if (!d_out || N < 0 || N > GBSH_MAX_N || !valid_single_precision(precision)) return GBSH_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (N == 0) {
-    static const double one[2] = {1.0, 0.0};
-    GBSH_CUDA(cudaMemcpyAsync(d_out, one, sizeof(one), cudaMemcpyHostToDevice, st));
-    if (d_abs_sum) GBSH_CUDA(cudaMemsetAsync(d_abs_sum, 0, sizeof(double), st));
+  if (N == 0) {  // lhaf = 1, written on the stream by a one-thread kernel
+    GBSH_CUDA(gbsh::launch_write_unit(reinterpret_cast<double2*>(d_out), d_abs_sum, st));
     return GBSH_OK;
   }
   if (!dA || lda < N || !workspace) return GBSH_EINVAL;
   if ((reinterpret_cast<uintptr_t>(workspace) & 255u) != 0) return GBSH_EINVAL;
   gbsh::LhafPlan plan;
-  int rc = plan_for(N, &plan);
+  int rc = plan_for(N, &plan, precision);
   if (rc != GBSH_OK) return rc;
   if (workspace_bytes < plan.bytes) return GBSH_EINVAL;
   GBSH_CUDA(gbsh::launch_lhaf(plan, reinterpret_cast<const double2*>(dA), lda, nullptr,
@@ -348,11 +381,16 @@ int gbsh_gbs_prob(const gbsh_c128* B, int M, int ldb, const gbsh_c128* gamma,
 
 int gbsh_subset_terms(const gbsh_c128* dA, int N, int lda, const uint64_t* d_z, int count,
                       gbsh_c128* d_out, void* stream) {
+  return gbsh_subset_terms_ex(dA, N, lda, GBSH_PREC_FP64, d_z, count, d_out, stream);
+}
+
+int gbsh_subset_terms_ex(const gbsh_c128* dA, int N, int lda, int precision, const uint64_t* d_z,
+                         int count, gbsh_c128* d_out, void* stream) {
   if (N < 1 || N > GBSH_MAX_N || !dA || lda < N || count < 0 || (count > 0 && (!d_z || !d_out)))
     return GBSH_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   gbsh::LhafPlan plan;
-  int rc = plan_for(N, &plan);
+  int rc = plan_for(N, &plan, precision);
   if (rc != GBSH_OK) return rc;
   int dev = 0;
   GBSH_CUDA(cudaGetDevice(&dev));
@@ -502,7 +540,8 @@ int gbsh_gbs_prob_batch(const gbsh_c128* B, int M, int ldb, const gbsh_c128* gam
 }
 
 int gbsh_set_batch_tuning(int precision, int n_max, int warps_per_cta) {
-  if (precision != GBSH_PREC_FP64 && precision != GBSH_PREC_C32 && precision != GBSH_PREC_DD)
+  if (precision != GBSH_PREC_FP64 && precision != GBSH_PREC_C32 && precision != GBSH_PREC_DD &&
+      precision != GBSH_PREC_TF)
     return GBSH_EINVAL;
   if (n_max < 0 || n_max > gbsh::kMaxN / 2 || warps_per_cta < 0 || warps_per_cta > gbsh::kMaxWarps)
     return GBSH_EINVAL;

@@ -32,8 +32,10 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
+#include "lhaf_tf.cuh"
 #include "lhaf_types.cuh"
 
 namespace gbsh {
@@ -271,15 +273,44 @@ template <> struct Cx<float2> {
   }
 };
 
+template <> struct Cx<tfc> {
+  using R = tf3;
+  __device__ __forceinline__ static tfc make(tf3 a, tf3 b) { return tfc{a, b}; }
+  __device__ __forceinline__ static tfc from(double2 v) { return tfc{tf3(v.x), tf3(v.y)}; }
+  __device__ __forceinline__ static double2 to_d(tfc v) {
+    double h, l;
+    tf_to_dd(v.x, h, l);
+    double h2, l2;
+    tf_to_dd(v.y, h2, l2);
+    return make_double2(h + l, h2 + l2);
+  }
+  __device__ __forceinline__ static Term to_term(tfc v) {
+    Term t;
+    tf_to_dd(v.x, t.re_hi, t.re_lo);
+    tf_to_dd(v.y, t.im_hi, t.im_lo);
+    return t;
+  }
+  __device__ __forceinline__ static tfc scale2(tfc v, int s) {
+    return tfc{tf_scale2(v.x, s), tf_scale2(v.y, s)};
+  }
+};
+__device__ __forceinline__ tf3 rfma(tf3 a, tf3 b, tf3 c) { return tf_fma(a, b, c); }
+
 // 1/k for k = 0..63 (entry 0 unused), filled by the host with correctly rounded values.
 // Defined here because this header is included by exactly one translation unit.
 __constant__ double c_inv_int[64];
+// 1/k as three FP32 words (a + b + c within 2^-90 of 1/k), filled by the host from an
+// exact integer division.
+__constant__ float c_inv_tf[64][3];
 
 // 1/k in the real type R of the per-subset arithmetic (exact to that type's precision).
 template <class R> __device__ __forceinline__ R inv_int(int k);
 template <> __device__ __forceinline__ double inv_int<double>(int k) { return c_inv_int[k]; }
 template <> __device__ __forceinline__ float inv_int<float>(int k) { return (float)c_inv_int[k]; }
 template <> __device__ __forceinline__ dd inv_int<dd>(int k) { return dd_recip(dd((double)k)); }
+template <> __device__ __forceinline__ tf3 inv_int<tf3>(int k) {
+  return tf3(c_inv_tf[k][0], c_inv_tf[k][1], c_inv_tf[k][2]);
+}
 
 // Compensated (two-sum) accumulator for the signed subset sum.
 struct DDAcc {
@@ -384,7 +415,8 @@ __device__ __forceinline__ void column_update(T* __restrict__ H, int ldh, int S,
 // p_Z for subset z (bit j <=> pair (j, j+n) in Z) with k = popcount(z) >= 1.
 // `area` is this warp's shared work area (warp_area_elems(k, n) elements of T at least).
 // T is the per-subset complex type: double2 (FP64 path) or float2 (reduced-precision
-// variant, whose terms are still accumulated in compensated FP64 by the caller).
+// variant, whose terms are still accumulated in compensated FP64 by the caller), ddc
+// (double-double) or tfc (triple-float, the accurate path: see lhaf_tf.cuh).
 // All 32 lanes must call it; every lane returns the same value.
 // ------------------------------------------------------------------------------------
 template <class T>
@@ -454,6 +486,24 @@ __device__ __noinline__ Term subset_term_full(const Problem& P, uint64_t z, int 
       if (mk > best) { best = mk; brow = r; }
     }
     unsigned mx = __reduce_max_sync(FULL, best);
+    if constexpr (std::is_same<T, tfc>::value) {
+      // A column whose candidates are all below 2^-kZeroBits of the column's largest entry
+      // is rounding residue of an exact cancellation (repeated rows and columns of a
+      // pattern with repeated modes produce these): pivoting on the residue applies
+      // multipliers that are ratios of rounding noise, which costs about 20 of the
+      // format's 72 bits on such subsets. It is treated as zero instead -- a perturbation of
+      // the column at 2^-kZeroBits of its scale, below the precision the subset sum needs.
+      // Keys compare FP32 bit patterns, so 2^-64 is 64 << 23 in the key.
+      constexpr unsigned kZeroBits = 64u;
+      unsigned cm = 0u;
+      for (int r = lane; r <= c; r += 32) {
+        const unsigned k2 = mag_key(H[r * ldh + c]);
+        cm = k2 > cm ? k2 : cm;
+      }
+      cm = __reduce_max_sync(FULL, cm);
+      cm = cm > mx ? cm : mx;
+      if (cm >= (kZeroBits << 23) && mx < cm - (kZeroBits << 23)) mx = 0u;
+    }
     if (mx == 0u) {  // zero subdiagonal: nothing to eliminate or scale
       zmask |= 1ull << c;
       if (lane == 0) kexp[c] = 0;
@@ -521,9 +571,34 @@ __device__ __noinline__ Term subset_term_full(const Problem& P, uint64_t z, int 
     }
   }
   __syncwarp();
+  // Triple-float words have the FP32 exponent range (and lose their low words below about
+  // 2^-78), so the triple-float path may evaluate the polynomials in mu = lambda / 2^sig,
+  // i.e. of 2^sig H, an exact rescaling. La Budde's factors C(a,b) and diagonal entries
+  // grow by at most 2^g per degree (g = max over factors of ceil(e / (b-a+1)), 2^e bounding
+  // |C(a,b)|; integer instructions on the exponents only). Over the <= 31 degrees kept, a
+  // growth within 2^-3 .. 2^3 per degree leaves every coefficient inside the safe window,
+  // so sig is 0 for such matrices and only pulls g back to that band otherwise (e.g. the
+  // all-ones matrices, g ~ 8 at N = 56). The power series are rescaled separately below,
+  // from the coefficients' own sizes.
+  int sig = 0;
+  if constexpr (std::is_same<T, tfc>::value) {
+    int g = -(1 << 20);
+    for (int e = lane; e < S * S; e += 32) {
+      const int a = e / S, bb = e - a * S;
+      if (a > bb || mag_key(H[a * ldh + bb]) == 0u) continue;
+      const int len = bb - a + 1;
+      if (a < bb && ((zmask >> a) & ((1ull << (bb - a)) - 1ull)) != 0ull) continue;
+      const int eb = pow2_exponent(H[a * ldh + bb]) + 2 + (a < bb ? kexp[bb] - kexp[a] : 0);
+      const int q = eb >= 0 ? (eb + len - 1) / len : -((-eb) / len);
+      g = q > g ? q : g;
+    }
+    g = __reduce_max_sync(FULL, g);
+    sig = g == -(1 << 20) ? 0 : (g > 3 ? 3 - g : (g < -3 ? -3 - g : 0));
+  }
   for (int e = lane; e < S * S; e += 32) {
     const int a = e / S, bb = e - a * S;
-    if (a < bb) H[a * ldh + bb] = Cx<T>::scale2(H[a * ldh + bb], kexp[bb] - kexp[a]);
+    if (a < bb) H[a * ldh + bb] = Cx<T>::scale2(H[a * ldh + bb], kexp[bb] - kexp[a] + sig * (bb - a + 1));
+    else if (a == bb && sig != 0) H[a * ldh + a] = Cx<T>::scale2(H[a * ldh + a], sig);
   }
   __syncwarp();
 
@@ -567,8 +642,28 @@ __device__ __noinline__ Term subset_term_full(const Problem& P, uint64_t z, int 
   const T zero = Cx<T>::make(R(0), R(0));
   // P_{S-1} and P_S have degree >= D here only if S-1 >= D; lanes above their degree read 0
   const int degM = (S - 1) < D ? (S - 1) : D, degK = S < D ? S : D;
-  const T qM = (lane <= degM) ? Pl[poly_offset(S - 1, D) + lane] : zero;
-  const T qK = (lane <= degK) ? Pl[poly_offset(S, D) + lane] : zero;
+  T qM = (lane <= degM) ? Pl[poly_offset(S - 1, D) + lane] : zero;
+  T qK = (lane <= degK) ? Pl[poly_offset(S, D) + lane] : zero;
+  if constexpr (std::is_same<T, tfc>::value) {
+    // Series rescaling (triple-float path): the traces and exp-polynomial values grow like
+    // rho^j with rho the spectral radius (all-ones matrices: 2^120 and more at N = 46), so
+    // the series runs on q(2^sig2 mu) with sig2 from the bound rho <= 2 max_d |q_d|^{1/d}
+    // (Fujiwara), which puts every root within 2 of the origin. Exact scaling by 2^{sig2 d}.
+    int g2 = -(1 << 20);
+    if (lane >= 1 && lane <= D) {
+      const int ek = mag_key(qK) ? pow2_exponent(qK) + 2 : -(1 << 20);
+      const int em = mag_key(qM) ? pow2_exponent(qM) + 2 : -(1 << 20);
+      const int e = ek > em ? ek : em;
+      if (e > -(1 << 20)) g2 = e >= 0 ? (e + lane - 1) / lane : -((-e) / lane);
+    }
+    g2 = __reduce_max_sync(FULL, g2);
+    const int sig2 = g2 == -(1 << 20) ? 0 : -g2;
+    if (sig2 != 0) {
+      qM = Cx<T>::scale2(qM, sig2 * lane);
+      qK = Cx<T>::scale2(qK, sig2 * lane);
+      sig += sig2;
+    }
+  }
   // (a) r = qK / qM   (qM_0 = 1)
   T r = qK;
   for (int s = 0; s < D; ++s) {
@@ -576,9 +671,11 @@ __device__ __noinline__ Term subset_term_full(const Problem& P, uint64_t z, int 
     T qs = shfl_up_c(qM, s);
     if (lane > s) r = cfms(r, qs, rs);
   }
-  // loop terms l_j = -r_{j+1}
+  // loop terms l_j = -r_{j+1} (for sig != 0: r of the rescaled matrices, whose loop terms
+  // carry one factor 2^sig more than the traces of the same degree)
   T lj = shfl_down_c(r, 1);
   lj = Cx<T>::make(-lj.x, -lj.y);
+  if (sig != 0) lj = Cx<T>::scale2(lj, -sig);
   // (b) power traces t_j = tr(M^j):  t_j = -j q_j - sum_{i=1}^{j-1} q_i t_{j-i}
   T tr = cscale(qM, -(R)lane);
   for (int s = 1; s < n; ++s) {
@@ -602,7 +699,12 @@ __device__ __noinline__ Term subset_term_full(const Problem& P, uint64_t z, int 
   }
   T pn = cscale(shfl_c(acc, n), inv_int<R>(n));
   __syncwarp();
-  return Cx<T>::to_term(pn);
+  Term out = Cx<T>::to_term(pn);
+  if (sig != 0) {  // [mu^n] = 2^{sig n} [lambda^n]: undo exactly in FP64
+    const int s2 = -sig * n;
+    out = Term{ldexp(out.re_hi, s2), ldexp(out.re_lo, s2), ldexp(out.im_hi, s2), ldexp(out.im_lo, s2)};
+  }
+  return out;
 }
 
 // p_Z rounded to complex double.

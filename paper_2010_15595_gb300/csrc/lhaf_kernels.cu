@@ -11,6 +11,7 @@
 //
 // The result depends only on the chunking (a function of N), not on the launch shape or
 // on which warp took which chunk, so it is bit-reproducible.
+#include <cmath>
 #include <mutex>
 
 #include "lhaf_core.cuh"
@@ -48,15 +49,17 @@ __global__ void expand_problem_kernel(const double2* __restrict__ base, int ld,
 
 // ------------------------------------------------------------------ subset sum
 // kVisit = true replaces the per-subset term by a visit count (enumeration check).
-template <bool kVisit>
+// T: complex type of the per-subset arithmetic (double2, or tfc for the triple-float path).
+template <class T, bool kVisit>
 __global__ void __launch_bounds__(32 * kMaxWarps, 1)
 lhaf_subsets_kernel(Problem P, int k_lo, int k_hi, int area_elems, uint64_t chunk_size,
                     unsigned nchunks, unsigned* __restrict__ counter,
                     double* __restrict__ partials, unsigned* __restrict__ visits) {
-  extern __shared__ double2 smem[];
+  extern __shared__ double2 smem_raw[];
+  T* smem = reinterpret_cast<T*>(smem_raw);
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  double2* area = smem + (size_t)warp * area_elems;
+  T* area = smem + (size_t)warp * area_elems;
   const int n = P.n;
 
   for (;;) {
@@ -68,16 +71,16 @@ lhaf_subsets_kernel(Problem P, int k_lo, int k_hi, int area_elems, uint64_t chun
     acc.zero();
     const uint64_t i0 = (uint64_t)ch * chunk_size, i1 = i0 + chunk_size;
     for (uint64_t i = i0; i < i1; ++i) {
-      const uint64_t z = i ^ (i >> 1);  // Gray code: consecutive subsets differ by one pair
+      const uint64_t z = i ^ (i >> 1);  // Gray-code order of the chunk's indices
       const int k = __popcll(z);
       if (k < k_lo || k > k_hi || k == 0) continue;
       if (kVisit) {
         if (lane == 0) atomicAdd(visits + z, 1u);
         continue;
       }
-      double2 pz = subset_term<double2>(P, z, k, area, lane);
-      if ((n - k) & 1) pz = make_double2(-pz.x, -pz.y);
-      acc.add(pz);
+      Term t = subset_term_full<T>(P, z, k, area, lane);
+      if ((n - k) & 1) t = Term{-t.re_hi, -t.re_lo, -t.im_hi, -t.im_lo};
+      acc.add(t);
     }
     if (!kVisit && lane == 0) {
       double* o = partials + (size_t)ch * 5;
@@ -87,19 +90,21 @@ lhaf_subsets_kernel(Problem P, int k_lo, int k_hi, int area_elems, uint64_t chun
 }
 
 // p_Z for a list of subsets (debug / sampled parity). One warp per listed subset.
+template <class T>
 __global__ void __launch_bounds__(32 * kMaxWarps, 1)
 subset_terms_kernel(Problem P, int area_elems, const uint64_t* __restrict__ zs, int count,
                     double2* __restrict__ out) {
-  extern __shared__ double2 smem[];
+  extern __shared__ double2 smem_raw[];
+  T* smem = reinterpret_cast<T*>(smem_raw);
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int wpb = blockDim.x >> 5;
-  double2* area = smem + (size_t)warp * area_elems;
+  T* area = smem + (size_t)warp * area_elems;
   for (int q = blockIdx.x * wpb + warp; q < count; q += gridDim.x * wpb) {
     const uint64_t z = zs[q];
     const int k = __popcll(z);
     double2 pz = make_double2(P.n == 0 ? 1.0 : 0.0, 0.0);
-    if (k > 0) pz = subset_term<double2>(P, z, k, area, lane);
+    if (k > 0) pz = subset_term<T>(P, z, k, area, lane);
     if (lane == 0) out[q] = pz;
   }
 }
@@ -298,14 +303,23 @@ cudaError_t device_info(DeviceInfo* info) {
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(lhaf_subsets_kernel<false>,
+    e = cudaFuncSetAttribute(lhaf_subsets_kernel<double2, false>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, d.smem_optin);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(lhaf_subsets_kernel<true>,
+    e = cudaFuncSetAttribute(lhaf_subsets_kernel<double2, true>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, d.smem_optin);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(subset_terms_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             d.smem_optin);
+    e = cudaFuncSetAttribute(lhaf_subsets_kernel<tfc, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, d.smem_optin);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(subset_terms_kernel<double2>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, d.smem_optin);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(subset_terms_kernel<tfc>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, d.smem_optin);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(lhaf_batch_kernel<tfc>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, d.smem_optin);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(lhaf_batch_kernel<double2>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, d.smem_optin);
@@ -334,21 +348,43 @@ cudaError_t ensure_constants() {
     for (int k = 1; k < 64; ++k) inv[k] = 1.0 / (double)k;
     e = cudaMemcpyToSymbol(c_inv_int, inv, sizeof(inv));
     if (e != cudaSuccess) return e;
+    // 1/k as three FP32 words: q = floor(2^100 / k) exactly, then its leading 24 bits, the
+    // next 24 bits and the next 24 bits (truncation keeps the words non-overlapping and of
+    // one sign; the value is within 2^-90 of 1/k).
+    float invt[64][3] = {};
+    for (int k = 1; k < 64; ++k) {
+      unsigned __int128 q = (((unsigned __int128)1) << 100) / (unsigned)k;
+      for (int w = 0; w < 3; ++w) {
+        if (q == 0) break;
+        int h = 127;
+        while (!((q >> h) & 1)) --h;
+        const int sh = h >= 23 ? h - 23 : 0;
+        const unsigned long long top = (unsigned long long)(q >> sh);
+        invt[k][w] = std::ldexp((float)top, sh - 100);
+        q -= ((unsigned __int128)top) << sh;
+      }
+    }
+    e = cudaMemcpyToSymbol(c_inv_tf, invt, sizeof(invt));
+    if (e != cudaSuccess) return e;
     g_const_done[dev] = true;
   }
   return cudaSuccess;
 }
 
 bool make_plan(int N, const DeviceInfo& dev, int warps_main, int kcap_override, LhafPlan* p,
-               unsigned max_chunks) {
+               unsigned max_chunks, int prec) {
   if (N < 1 || N > kMaxN) return false;
+  if (prec != kPrecFP64 && prec != kPrecTF) return false;
   LhafPlan plan{};
+  plan.prec = prec;
+  plan.esz = prec_elem_bytes(prec);
   plan.N = N;
   plan.Ne = N + (N & 1);
   plan.n = plan.Ne / 2;
   const int n = plan.n;
   const size_t limit = (size_t)dev.smem_optin;
-  auto area_bytes = [&](int k) { return (size_t)warp_area_elems(k, n) * sizeof(double2); };
+  const int esz = plan.esz;
+  auto area_bytes = [&](int k) { return (size_t)warp_area_elems(k, n, esz) * esz; };
   // largest popcount whose work area fits W warps per CTA (0 if none)
   auto kfit = [&](int W) {
     int kc = 0;
@@ -372,7 +408,7 @@ bool make_plan(int N, const DeviceInfo& dev, int warps_main, int kcap_override, 
     if (plan.nclass == 0 && kcap_override > 0 && kcap_override < kc) kc = kcap_override;
     if (kc > k_done) {
       if (plan.nclass == kMaxClasses) return false;
-      plan.cls[plan.nclass++] = ClassPlan{k_done + 1, kc, Wc, warp_area_elems(kc, n), 0};
+      plan.cls[plan.nclass++] = ClassPlan{k_done + 1, kc, Wc, warp_area_elems(kc, n, esz), 0};
       k_done = kc;
     }
   }
@@ -380,11 +416,13 @@ bool make_plan(int N, const DeviceInfo& dev, int warps_main, int kcap_override, 
   for (int c = 0; c < plan.nclass; ++c) {
     ClassPlan& cp = plan.cls[c];
     int per_sm = 0;
-    size_t smem = (size_t)cp.warps * cp.area_elems * sizeof(double2);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lhaf_subsets_kernel<false>,
-                                                      32 * cp.warps, smem) != cudaSuccess ||
-        per_sm < 1)
-      per_sm = 1;
+    size_t smem = (size_t)cp.warps * cp.area_elems * esz;
+    cudaError_t oe = prec == kPrecTF
+                         ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                               &per_sm, lhaf_subsets_kernel<tfc, false>, 32 * cp.warps, smem)
+                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                               &per_sm, lhaf_subsets_kernel<double2, false>, 32 * cp.warps, smem);
+    if (oe != cudaSuccess || per_sm < 1) per_sm = 1;
     cp.blocks = per_sm * dev.sm_count;
   }
   const uint64_t total = (uint64_t)1 << n;
@@ -478,10 +516,15 @@ static cudaError_t launch_classes(const LhafPlan& plan, void* ws, unsigned* visi
     cudaStream_t sc = c == 0 ? stream : side[c];
     if (c > 0) e = cudaStreamWaitEvent(sc, fork, 0);
     if (e != cudaSuccess) break;
-    size_t smem = (size_t)cp.warps * cp.area_elems * sizeof(double2);
-    lhaf_subsets_kernel<kVisit><<<cp.blocks, 32 * cp.warps, smem, sc>>>(
-        P, cp.k_lo, cp.k_hi, cp.area_elems, plan.chunk_size, plan.nchunks, counters + c,
-        partials + (size_t)c * plan.nchunks * 5, visits);
+    const size_t smem = (size_t)cp.warps * cp.area_elems * plan.esz;
+    if (!kVisit && plan.prec == kPrecTF)
+      lhaf_subsets_kernel<tfc, false><<<cp.blocks, 32 * cp.warps, smem, sc>>>(
+          P, cp.k_lo, cp.k_hi, cp.area_elems, plan.chunk_size, plan.nchunks, counters + c,
+          partials + (size_t)c * plan.nchunks * 5, visits);
+    else
+      lhaf_subsets_kernel<double2, kVisit><<<cp.blocks, 32 * cp.warps, smem, sc>>>(
+          P, cp.k_lo, cp.k_hi, cp.area_elems, plan.chunk_size, plan.nchunks, counters + c,
+          partials + (size_t)c * plan.nchunks * 5, visits);
     e = cudaGetLastError();
     if (e == cudaSuccess && c > 0) {
       cudaEvent_t join = nullptr;
@@ -517,17 +560,30 @@ cudaError_t launch_subset_terms(const LhafPlan& plan, const double2* base, int l
   if (e != cudaSuccess) return e;
   if (count <= 0) return cudaSuccess;
   // every listed subset may be the full set: size the area for k = n
-  const int area = warp_area_elems(plan.n, plan.n);
+  const int area = warp_area_elems(plan.n, plan.n, plan.esz);
   DeviceInfo dev;
   e = device_info(&dev);
   if (e != cudaSuccess) return e;
-  int W = (int)((size_t)dev.smem_optin / (area * sizeof(double2)));
+  int W = (int)((size_t)dev.smem_optin / ((size_t)area * plan.esz));
   if (W > 4) W = 4;
   if (W < 1) return cudaErrorInvalidValue;
   int blocks = (count + W - 1) / W;
   if (blocks > 4 * dev.sm_count) blocks = 4 * dev.sm_count;
-  subset_terms_kernel<<<blocks, 32 * W, (size_t)W * area * sizeof(double2), stream>>>(
-      problem_of(plan, ws), area, z, count, out);
+  const size_t smem = (size_t)W * area * plan.esz;
+  if (plan.prec == kPrecTF)
+    subset_terms_kernel<tfc><<<blocks, 32 * W, smem, stream>>>(problem_of(plan, ws), area, z, count, out);
+  else
+    subset_terms_kernel<double2><<<blocks, 32 * W, smem, stream>>>(problem_of(plan, ws), area, z, count, out);
+  return cudaGetLastError();
+}
+
+__global__ void write_unit_kernel(double2* __restrict__ out, double* __restrict__ abs_sum) {
+  out[0] = make_double2(1.0, 0.0);
+  if (abs_sum) abs_sum[0] = 0.0;
+}
+
+cudaError_t launch_write_unit(double2* out, double* abs_sum, cudaStream_t stream) {
+  write_unit_kernel<<<1, 1, 0, stream>>>(out, abs_sum);
   return cudaGetLastError();
 }
 
@@ -557,6 +613,8 @@ static int batch_blocks_per_sm(int precision, int W, size_t smem) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lhaf_batch_kernel<float2>, 32 * W, smem);
   } else if (precision == kPrecDD) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lhaf_batch_kernel<ddc>, 32 * W, smem);
+  } else if (precision == kPrecTF) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lhaf_batch_kernel<tfc>, 32 * W, smem);
   } else {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lhaf_batch_kernel<double2>, 32 * W, smem);
   }
@@ -577,6 +635,9 @@ static cudaError_t launch_batch_class(const BatchProblem* d_prob, int count, uns
         d_prob, count, total_chunks, k_lo, k_hi, area, d_counter, d_partials);
   } else if (precision == kPrecDD) {
     lhaf_batch_kernel<ddc><<<blocks, 32 * W, smem, stream>>>(
+        d_prob, count, total_chunks, k_lo, k_hi, area, d_counter, d_partials);
+  } else if (precision == kPrecTF) {
+    lhaf_batch_kernel<tfc><<<blocks, 32 * W, smem, stream>>>(
         d_prob, count, total_chunks, k_lo, k_hi, area, d_counter, d_partials);
   } else {
     lhaf_batch_kernel<double2><<<blocks, 32 * W, smem, stream>>>(

@@ -24,6 +24,8 @@ struct ClassPlan {
 // Everything needed to evaluate one loop hafnian of padded size Ne.
 struct LhafPlan {
   int N, Ne, n;
+  int prec;  // kPrecFP64 or kPrecTF: the per-subset arithmetic
+  int esz;   // bytes of one complex element of that arithmetic
   int nclass;
   ClassPlan cls[kMaxClasses];
   unsigned nchunks;
@@ -42,15 +44,20 @@ cudaError_t device_info(DeviceInfo* info);
 // Uploads constant tables on the current device (once per device).
 cudaError_t ensure_constants();
 // Builds the launch plan. warps_main = 0 selects the default cap on warps per CTA;
-// max_chunks bounds the number of subset chunks (a power of two). Returns false if N is out
-// of range for the available shared memory.
+// max_chunks bounds the number of subset chunks (a power of two); prec selects the
+// per-subset arithmetic (kPrecFP64 or kPrecTF). Returns false if N or prec is out of range
+// for the available shared memory.
 bool make_plan(int N, const DeviceInfo& dev, int warps_main, int kcap_override, LhafPlan* plan,
-               unsigned max_chunks = kTargetChunks);
+               unsigned max_chunks = kTargetChunks, int prec = kPrecFP64);
 
 // Launches expansion + subset classes + finalize for one problem. `base`, `diag`, `idx` as
 // in expand_problem_kernel. Writes lhaf (re, im) and sum |p_Z| into ws + off_out.
 cudaError_t launch_lhaf(const LhafPlan& plan, const double2* base, int ld, const double2* diag,
                         const int* idx, void* ws, cudaStream_t stream);
+
+// Writes lhaf = 1 (the empty matrix) to out[0] and 0 to *abs_sum (if not null) with a
+// one-thread kernel on `stream`.
+cudaError_t launch_write_unit(double2* out, double* abs_sum, cudaStream_t stream);
 
 // Debug: p_Z of `count` subsets (device z list) of an already expanded problem.
 cudaError_t launch_subset_terms(const LhafPlan& plan, const double2* base, int ld,

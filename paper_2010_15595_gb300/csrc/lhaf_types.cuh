@@ -41,10 +41,12 @@ struct BatchInput {
 constexpr int kPrecFP64 = 0;
 constexpr int kPrecC32 = 1;
 constexpr int kPrecDD = 3;  // double-double per subset (value 2 is the API's mixed mode)
+constexpr int kPrecTF = 4;  // triple-float per subset (three FP32 words, ~72-bit significand)
+constexpr int kNumPrec = 5;
 
 // Bytes of one complex element of the per-subset arithmetic of a precision.
 __host__ __device__ inline int prec_elem_bytes(int precision) {
-  return precision == kPrecC32 ? 8 : (precision == kPrecDD ? 32 : 16);
+  return precision == kPrecC32 ? 8 : (precision == kPrecDD ? 32 : (precision == kPrecTF ? 24 : 16));
 }
 
 // Chunk size of a batched problem with n pairs: a function of n alone.

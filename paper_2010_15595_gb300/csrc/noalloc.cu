@@ -33,6 +33,23 @@ int fail(cudaError_t e) {
   return e == cudaErrorMemoryAllocation ? GBSH_ENOMEM : GBSH_ECUDA;
 }
 
+// The library default plan for size N, with the chunk count halved until the scratch fits
+// the fixed array: GBSH_OK, or GBSH_ENOMEM when even one chunk does not fit.
+int fit_plan(int N, gbsh::LhafPlan* plan) {
+  gbsh::DeviceInfo info;
+  cudaError_t e = gbsh::device_info(&info);
+  if (e != cudaSuccess) return fail(e);
+  e = gbsh::ensure_constants();
+  if (e != cudaSuccess) return fail(e);
+  unsigned max_chunks = gbsh::kTargetChunks;
+  for (;;) {
+    if (!gbsh::make_plan(N, info, 0, 0, plan, max_chunks)) return GBSH_EINVAL;
+    if (plan->bytes <= (size_t)GBSH_NOALLOC_SCRATCH_BYTES) return GBSH_OK;
+    if (plan->nchunks <= 1u) return GBSH_ENOMEM;
+    max_chunks = plan->nchunks / 2;
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -42,14 +59,10 @@ int gbsh_lhaf_noalloc(const gbsh_c128* dA, int N, int lda, gbsh_c128* d_out, dou
   if (!d_out || N < 0 || N > GBSH_MAX_N) return GBSH_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (N == 0) {
-    // lhaf of the empty matrix is 1; written with plain copies from host constants
-    static const double one[2] = {1.0, 0.0};
-    cudaError_t e = cudaMemcpyAsync(d_out, one, sizeof(one), cudaMemcpyHostToDevice, st);
+    // lhaf of the empty matrix is 1, written by a one-thread kernel on the stream (no host
+    // memory involved, so the call stays asynchronous)
+    cudaError_t e = gbsh::launch_write_unit(reinterpret_cast<double2*>(d_out), d_abs_sum, st);
     if (e != cudaSuccess) return fail(e);
-    if (d_abs_sum) {
-      e = cudaMemsetAsync(d_abs_sum, 0, sizeof(double), st);
-      if (e != cudaSuccess) return fail(e);
-    }
     return GBSH_OK;
   }
   if (!dA || lda < N) return GBSH_EINVAL;
@@ -71,20 +84,9 @@ int gbsh_lhaf_noalloc(const gbsh_c128* dA, int N, int lda, gbsh_c128* d_out, dou
     scratch = g_scratch_ptr[dev];
   }
 
-  gbsh::DeviceInfo info;
-  e = gbsh::device_info(&info);
-  if (e != cudaSuccess) return fail(e);
-  e = gbsh::ensure_constants();
-  if (e != cudaSuccess) return fail(e);
-  // The library default plan, with the chunk count halved until the scratch fits.
   gbsh::LhafPlan plan;
-  unsigned max_chunks = gbsh::kTargetChunks;
-  for (;;) {
-    if (!gbsh::make_plan(N, info, 0, 0, &plan, max_chunks)) return GBSH_EINVAL;
-    if (plan.bytes <= (size_t)GBSH_NOALLOC_SCRATCH_BYTES) break;
-    if (plan.nchunks <= 1u) return GBSH_ENOMEM;
-    max_chunks = plan.nchunks / 2;
-  }
+  int rc = fit_plan(N, &plan);
+  if (rc != GBSH_OK) return rc;
 
   // The chunk counters are zeroed inside launch_lhaf; every other scratch byte the
   // kernels read is written earlier in the same launch sequence.
@@ -100,6 +102,14 @@ int gbsh_lhaf_noalloc(const gbsh_c128* dA, int N, int lda, gbsh_c128* d_out, dou
     if (e != cudaSuccess) return fail(e);
   }
   return GBSH_OK;
+}
+
+int gbsh_lhaf_noalloc_plan(int N, int* nchunks) {
+  if (N < 1 || N > GBSH_MAX_N) return GBSH_EINVAL;
+  gbsh::LhafPlan plan;
+  const int rc = fit_plan(N, &plan);
+  if (rc == GBSH_OK && nchunks) *nchunks = (int)plan.nchunks;
+  return rc;
 }
 
 }  // extern "C"

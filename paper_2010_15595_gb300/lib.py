@@ -17,7 +17,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libgbsh.so")
 
 GBSH_OK, GBSH_EINVAL, GBSH_ENOMEM, GBSH_ECUDA, GBSH_ETIMEOUT, GBSH_PENDING, GBSH_ENOTFOUND = range(7)
 MAX_N = 60
-PREC_FP64, PREC_C32, PREC_MIXED, PREC_DD = 0, 1, 2, 3
+NOALLOC_SCRATCH_BYTES = 8 << 20  # GBSH_NOALLOC_SCRATCH_BYTES
+PREC_FP64, PREC_C32, PREC_MIXED, PREC_DD, PREC_TF = 0, 1, 2, 3, 4
 # Largest N for which the complex-FP32 per-subset variant is enabled (GBSH_C32_MAX_N): its
 # measured error against the FP64 path stays <= 1e-5 relative up to this size.
 C32_MAX_N = 4
@@ -59,7 +60,13 @@ def load() -> ctypes.CDLL:
         "gbsh_visit_counts": ([i, vp, vp], i),
         "gbsh_set_lhaf_tuning": ([i, i], i),
         "gbsh_lhaf_plan": ([i] + [ctypes.POINTER(ctypes.c_int)] * 5, i),
+        "gbsh_lhaf_ex": ([vp, i, i, i, pc, pd, vp], i),
+        "gbsh_lhaf_async_ex": ([vp, i, i, i, vp, vp, vp, sz, vp], i),
+        "gbsh_lhaf_workspace_size_ex": ([i, i], sz),
+        "gbsh_subset_terms_ex": ([vp, i, i, i, vp, i, vp, vp], i),
+        "gbsh_lhaf_plan_ex": ([i, i] + [ctypes.POINTER(ctypes.c_int)] * 5, i),
         "gbsh_lhaf_noalloc": ([vp, i, i, vp, vp, vp], i),
+        "gbsh_lhaf_noalloc_plan": ([i, ctypes.POINTER(ctypes.c_int)], i),
         "gbsh_lhaf_batch": ([vp, vp, vp, i, vp, vp, i, vp], i),
         "gbsh_gbs_prob_batch": ([vp, i, i, vp, ctypes.c_int64, vp, i, vp, vp, vp, i, vp], i),
         "gbsh_set_batch_tuning": ([i, i, i], i),
@@ -79,7 +86,9 @@ def exported_symbols():
             "gbsh_lhaf_async", "gbsh_gbs_prob", "gbsh_subset_terms", "gbsh_visit_counts",
             "gbsh_set_lhaf_tuning", "gbsh_lhaf_plan", "gbsh_lhaf_noalloc", "gbsh_lhaf_batch",
             "gbsh_gbs_prob_batch", "gbsh_set_batch_tuning", "gbsh_set_batch_graphs",
-            "gbsh_batch_graph_stats"]
+            "gbsh_batch_graph_stats", "gbsh_lhaf_ex", "gbsh_lhaf_async_ex",
+            "gbsh_lhaf_workspace_size_ex", "gbsh_subset_terms_ex", "gbsh_lhaf_plan_ex",
+            "gbsh_lhaf_noalloc_plan"]
 
 
 def _strerror(code: int) -> str:
@@ -129,40 +138,58 @@ def set_tuning(warps_per_cta: int = 0, kcap: int = 0):
     _check(load().gbsh_set_lhaf_tuning(warps_per_cta, kcap), "gbsh_set_lhaf_tuning")
 
 
-def lhaf(A, stream=None, return_error=False):
-    """Loop hafnian of a square complex matrix (numpy array or torch tensor, host or CUDA)."""
+def lhaf(A, stream=None, return_error=False, precision=None):
+    """Loop hafnian of a square complex matrix (numpy array or torch tensor, host or CUDA).
+    precision: None (gbsh_lhaf, FP64), PREC_FP64 or PREC_TF (gbsh_lhaf_ex)."""
     ptr, N, ld, keep = _as_matrix(A)
     out = C128()
     err = ctypes.c_double()
-    rc = load().gbsh_lhaf(ctypes.c_void_p(ptr if N else 0), N, max(ld, N), ctypes.byref(out),
-                          ctypes.byref(err), ctypes.c_void_p(_stream_handle(stream)))
-    _check(rc, "gbsh_lhaf")
+    st = ctypes.c_void_p(_stream_handle(stream))
+    if precision is None:
+        rc = load().gbsh_lhaf(ctypes.c_void_p(ptr if N else 0), N, max(ld, N), ctypes.byref(out),
+                              ctypes.byref(err), st)
+        _check(rc, "gbsh_lhaf")
+    else:
+        rc = load().gbsh_lhaf_ex(ctypes.c_void_p(ptr if N else 0), N, max(ld, N), int(precision),
+                                 ctypes.byref(out), ctypes.byref(err), st)
+        _check(rc, "gbsh_lhaf_ex")
     val = complex(out.re, out.im)
     return (val, err.value) if return_error else val
 
 
-def plan(N: int) -> dict:
+def plan(N: int, precision=None) -> dict:
     """Launch plan of an N x N evaluation on the current device (see gbsh_lhaf_plan)."""
     vals = [ctypes.c_int() for _ in range(5)]
-    _check(load().gbsh_lhaf_plan(N, *[ctypes.byref(v) for v in vals]), "gbsh_lhaf_plan")
+    refs = [ctypes.byref(v) for v in vals]
+    if precision is None:
+        _check(load().gbsh_lhaf_plan(N, *refs), "gbsh_lhaf_plan")
+    else:
+        _check(load().gbsh_lhaf_plan_ex(N, int(precision), *refs), "gbsh_lhaf_plan_ex")
     keys = ["nclass", "kernels", "warps", "kcap", "nchunks"]
     return {k: v.value for k, v in zip(keys, vals)}
 
 
-def workspace_size(N: int) -> int:
-    return int(load().gbsh_lhaf_workspace_size(N))
+def workspace_size(N: int, precision=None) -> int:
+    if precision is None:
+        return int(load().gbsh_lhaf_workspace_size(N))
+    return int(load().gbsh_lhaf_workspace_size_ex(N, int(precision)))
 
 
-def lhaf_async(dA, d_out, workspace, d_abs_sum=None, stream=None):
+def lhaf_async(dA, d_out, workspace, d_abs_sum=None, stream=None, precision=None):
     """Device-only variant: dA (CUDA complex128 N x N), d_out (CUDA complex128, >= 1 entry),
-    workspace (CUDA uint8 tensor of >= workspace_size(N) bytes). No synchronisation."""
+    workspace (CUDA uint8 tensor of >= workspace_size(N, precision) bytes). No
+    synchronisation. precision: None (gbsh_lhaf_async), PREC_FP64 or PREC_TF."""
     ptr, N, ld, _ = _as_matrix(dA)
-    rc = load().gbsh_lhaf_async(
-        ctypes.c_void_p(ptr), N, ld, ctypes.c_void_p(d_out.data_ptr()),
-        ctypes.c_void_p(d_abs_sum.data_ptr() if d_abs_sum is not None else 0),
-        ctypes.c_void_p(workspace.data_ptr()), workspace.numel() * workspace.element_size(),
-        ctypes.c_void_p(_stream_handle(stream)))
-    _check(rc, "gbsh_lhaf_async")
+    args = (ctypes.c_void_p(d_out.data_ptr()),
+            ctypes.c_void_p(d_abs_sum.data_ptr() if d_abs_sum is not None else 0),
+            ctypes.c_void_p(workspace.data_ptr()), workspace.numel() * workspace.element_size(),
+            ctypes.c_void_p(_stream_handle(stream)))
+    if precision is None:
+        rc = load().gbsh_lhaf_async(ctypes.c_void_p(ptr), N, ld, *args)
+        _check(rc, "gbsh_lhaf_async")
+    else:
+        rc = load().gbsh_lhaf_async_ex(ctypes.c_void_p(ptr), N, ld, int(precision), *args)
+        _check(rc, "gbsh_lhaf_async_ex")
 
 
 def lhaf_noalloc(dA, d_out, d_abs_sum=None, stream=None):
@@ -174,6 +201,13 @@ def lhaf_noalloc(dA, d_out, d_abs_sum=None, stream=None):
         ctypes.c_void_p(d_abs_sum.data_ptr() if d_abs_sum is not None else 0),
         ctypes.c_void_p(_stream_handle(stream)))
     _check(rc, "gbsh_lhaf_noalloc")
+
+
+def noalloc_chunks(N: int) -> int:
+    """Chunks gbsh_lhaf_noalloc uses for size N (raises GbshError(GBSH_ENOMEM) when none fit)."""
+    c = ctypes.c_int()
+    _check(load().gbsh_lhaf_noalloc_plan(N, ctypes.byref(c)), "gbsh_lhaf_noalloc_plan")
+    return c.value
 
 
 def gbs_prob(B, gamma, pattern, p_vac=1.0, stream=None, return_lhaf=False):
@@ -203,15 +237,22 @@ def gbs_prob(B, gamma, pattern, p_vac=1.0, stream=None, return_lhaf=False):
     return (prob.value, complex(lh.re, lh.im)) if return_lhaf else prob.value
 
 
-def subset_terms(dA, d_z, stream=None):
-    """p_Z for the subsets in d_z (CUDA uint64/int64 tensor); returns a CUDA complex128 tensor."""
+def subset_terms(dA, d_z, stream=None, precision=None):
+    """p_Z for the subsets in d_z (CUDA uint64/int64 tensor); returns a CUDA complex128 tensor.
+    precision: None (gbsh_subset_terms, FP64), PREC_FP64 or PREC_TF."""
     import torch
     ptr, N, ld, _ = _as_matrix(dA)
     out = torch.empty(d_z.numel(), dtype=torch.complex128, device=d_z.device)
-    rc = load().gbsh_subset_terms(ctypes.c_void_p(ptr), N, ld, ctypes.c_void_p(d_z.data_ptr()),
-                                  d_z.numel(), ctypes.c_void_p(out.data_ptr()),
-                                  ctypes.c_void_p(_stream_handle(stream)))
-    _check(rc, "gbsh_subset_terms")
+    st = ctypes.c_void_p(_stream_handle(stream))
+    if precision is None:
+        rc = load().gbsh_subset_terms(ctypes.c_void_p(ptr), N, ld, ctypes.c_void_p(d_z.data_ptr()),
+                                      d_z.numel(), ctypes.c_void_p(out.data_ptr()), st)
+        _check(rc, "gbsh_subset_terms")
+    else:
+        rc = load().gbsh_subset_terms_ex(ctypes.c_void_p(ptr), N, ld, int(precision),
+                                         ctypes.c_void_p(d_z.data_ptr()), d_z.numel(),
+                                         ctypes.c_void_p(out.data_ptr()), st)
+        _check(rc, "gbsh_subset_terms_ex")
     return out
 
 

@@ -87,6 +87,23 @@ def large_lhaf(N: int, seed: int = 0) -> np.ndarray:
     return with_diagonal(B, complex_normal(N, 0.1, rng))
 
 
+def block_diagonal_large(N1: int, N2: int, seed: int = 0):
+    """An N1+N2 matrix P (A1 (+) A2) P^T made of two independent large-config blocks
+    (large_lhaf of sizes N1 and N2, different seeds) under a seeded symmetric permutation P
+    of the rows and columns. Returns (A, A1, A2). Its loop hafnian is lhaf(A1) lhaf(A2)
+    (a perfect matching with loops of a block-diagonal graph pairs vertices inside blocks
+    only, and relabelling vertices leaves the sum unchanged), so a reference at N = 50 or 56
+    costs two evaluations of half the size."""
+    A1 = large_lhaf(N1, seed=2 * seed + 1)
+    A2 = large_lhaf(N2, seed=2 * seed + 2)
+    N = N1 + N2
+    D = np.zeros((N, N), dtype=np.complex128)
+    D[:N1, :N1] = A1
+    D[N1:, N1:] = A2
+    perm = rng_for(9, seed * 1000 + N).permutation(N)
+    return D[np.ix_(perm, perm)], A1, A2
+
+
 def random_symmetric_uniform(N: int, seed: int = 0) -> np.ndarray:
     """Timing side workload of Sec. IV (Fig. 3): Re and Im of every entry ~ U[0, 1], then
     symmetrised."""

@@ -140,21 +140,24 @@ def test_golden_n40(gbsh, name):
 
 
 def test_golden_n50(gbsh):
-    """N=50 (2^25 subsets) against the double oracle. The gate is measured rather than
-    assumed: the GPU's per-subset terms on the fixture's seeded sample of subsets are
-    compared with the oracle's terms, and the signed sum of 2^25 terms with independent
-    errors of that size has a random-walk error sqrt(2^n mean|e_Z|^2); the gate is 6 times
-    that (or the stated 1e-7, whichever is larger)."""
-    import torch
+    """N=50 (2^25 subsets), FP64 path, against the double oracle, at the FP64 gate: the
+    oracle's own sum of |p_Z|^2 sets it (no GPU output enters it)."""
     A, rec = _golden("lhaf_n50")
-    ref = complex(*rec["lhaf_d"])
+    ref = complex(*rec.get("lhaf_ld", rec["lhaf_d"]))
     got = gbsh.lhaf(_dev(A))
-    zs = np.array([t[0] for t in rec["terms"]], dtype=np.int64)
-    pz_ref = np.array([complex(t[1], t[2]) for t in rec["terms"]])
-    pz_gpu = gbsh.subset_terms(_dev(A), torch.from_numpy(zs).cuda()).cpu().numpy()
-    e2 = np.mean(np.abs(pz_gpu - pz_ref) ** 2)
-    gate = max(TOL_50, 6.0 * np.sqrt((2.0 ** 25) * e2) / abs(ref))
-    assert rel(got, ref) <= gate, (got, ref, rel(got, ref), gate)
+    assert rel(got, ref) <= fp64_tol(50, ref, rec["sq_sum"]), (got, ref, rel(got, ref))
+
+
+# The FP64 path held to the stated tolerance: it misses it at N >= 40 (measured 4.7e-8 at
+# N=40, 2.5e-7 for the repeated-mode N=40 matrix and 1.7e-5 at N=50), which is why the
+# triple-float path exists (tests/test_gpu_accurate.py carries the stated-tolerance claim).
+# strict: an FP64 result that unexpectedly met the tolerance would fail the suite too.
+@pytest.mark.xfail(strict=True, reason="FP64 per subset is above the stated tolerance at N >= 40")
+@pytest.mark.parametrize("name", ["lhaf_n40", "lhaf_n40_repeated"])
+def test_fp64_at_stated_tolerance_n40(gbsh, name):
+    A, rec = _golden(name)
+    ref = complex(*rec["lhaf_ld"])
+    assert rel(gbsh.lhaf(_dev(A)), ref) <= TOL_40
 
 
 @pytest.mark.parametrize("name", ["lhaf_n40", "lhaf_n50", "lhaf_n56"])
