@@ -4,10 +4,12 @@
 Workload (one step): the loop hafnian of one N=40 complex symmetric matrix per GPU --
 M=40 modes, Haar-random interferometer, squeezing r_i ~ U[0.4, 0.9], B = U diag(tanh r) U^T
 with the diagonal replaced by gamma_i ~ CN(0, 0.2^2) -- i.e. the 2^20 pair-subset terms of
-the subset formula. Metric: subset-terms per second (whole job), with the FP64 roofline
-fraction of the dominant kernel. Each rank evaluates its own seeded matrix (weak scaling,
-no data-path collective). A second, shorter measurement at N=50 (2^25 subsets) is
-reported under "n50".
+the subset formula. Metric: subset-terms per second (whole job). The headline path is the
+accurate one (triple-float per subset, which meets the stated relative tolerance), with the
+FP32-issue roofline fraction of its subset kernel; the FP64 path is timed beside it with its
+FP64 roofline fraction, and each path's error against the oracle's reference is reported.
+Each rank evaluates its own seeded matrix (weak scaling, no data-path collective). Shorter
+measurements at N=50 (2^25 subsets) are reported under "n50".
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -132,7 +134,8 @@ class ClockSampler:
 
 # Sources that define the subset kernel, its launches and its finalize (the sampler and the
 # C-ABI wrappers do not change what one evaluation moves through DRAM).
-KERNEL_SOURCES = ("lhaf_core.cuh", "lhaf_kernels.cu", "lhaf_kernels.cuh", "lhaf_types.cuh")
+KERNEL_SOURCES = ("lhaf_core.cuh", "lhaf_kernels.cu", "lhaf_kernels.cuh", "lhaf_types.cuh",
+                  "lhaf_tf.cuh")
 
 
 def kernel_source_hash() -> str:
@@ -144,19 +147,28 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(N: int):
-    """DRAM bytes of one evaluation (every launch of gbsh_lhaf: expansion, the popcount-class
-    launches of the subset kernel, the two finalize levels) from the committed ncu summary, if
-    it was taken on the current kernel sources; else None."""
-    path = os.path.join(ROOT, "profiles", "lhaf_subsets_dram_traffic.json")
+def recorded_traffic(N: int, path: str):
+    """DRAM bytes of one evaluation on `path` ("tf" or "fp64"): every launch of the evaluation
+    (expansion, the popcount-class launches of the subset kernel, the two finalize levels),
+    from the committed ncu summary, if it was taken on the current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", "lhaf_subsets_dram_traffic.json")
     try:
-        with open(path) as f:
+        with open(p) as f:
             rec = json.load(f)
     except (OSError, ValueError):
         return None
     if rec.get("kernel_source_hash") != kernel_source_hash():
         return None
-    return rec.get("bytes_per_evaluation", {}).get(str(N))
+    return rec.get("bytes_per_evaluation", {}).get(path, {}).get(str(N))
+
+
+def recorded_probes() -> dict:
+    """Throughput probe results committed under profiles/ (context beside derived peaks)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "alu_peak_probes.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
 
 
 # ------------------------------------------------------------------ CPU oracle timing
@@ -182,6 +194,40 @@ def time_oracle(A, target_s: float, rng_seed: int = 0):
 
 # ------------------------------------------------------------------ our arm
 
+def golden_reference(name):
+    """(matrix, reference value, kind) of a committed oracle fixture, or None. The long-double
+    oracle value where the fixture has one, else the double oracle's."""
+    import numpy as np
+    base = os.path.join(ROOT, "tests", "golden", name)
+    try:
+        with open(base + ".json") as f:
+            rec = json.load(f)
+        with open(base + ".matrix.txt") as f:
+            n = int(f.readline())
+            vals = np.array([float(t) for t in f.read().split()])
+    except (OSError, ValueError):
+        return None
+    A = (vals[0::2] + 1j * vals[1::2]).reshape(n, n)
+    if "lhaf_ld" in rec:
+        return A, complex(*rec["lhaf_ld"]), "long-double oracle"
+    return A, complex(*rec["lhaf_d"]), "double oracle (its own error is estimated at ~2e-7 here)"
+
+
+def rel_err(v, ref):
+    return abs(v - ref) / abs(ref) if ref is not None else None
+
+
+def host_cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return "unknown"
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -194,111 +240,185 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream()
     N = args.n
+    TF, F64 = lib.PREC_TF, lib.PREC_FP64
     A = workloads.single_lhaf_mid(N, seed=rank_seed(rank))
     dA = torch.from_numpy(A).to(dev)
-    ws = torch.empty(lib.workspace_size(N), dtype=torch.uint8, device=dev)
-    out = torch.empty(1, dtype=torch.complex128, device=dev)
-    asum = torch.empty(1, dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    plan = lib.plan(N)
+    ref40 = golden_reference("lhaf_n40") if (rank == 0 and N == 40) else None
 
-    def step():
-        lib.lhaf_async(dA, out, ws, d_abs_sum=asum, stream=stream)
+    def timed_path(prec, steps, warmup):
+        """Times `steps` evaluations of the step matrix in `prec` (CUDA events on the
+        launching stream, L2 flushed between steps outside the events)."""
+        ws = torch.empty(lib.workspace_size(N, prec), dtype=torch.uint8, device=dev)
+        out = torch.empty(1, dtype=torch.complex128, device=dev)
+        asum = torch.empty(1, dtype=torch.float64, device=dev)
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local_rank) as clocks:
-        t0 = time.perf_counter()
-        for e0, e1 in ev:
-            flush.zero_()  # L2 flush between timed steps (outside the events)
-            e0.record(stream)
+        def step():
+            lib.lhaf_async(dA, out, ws, d_abs_sum=asum, stream=stream, precision=prec)
+
+        for _ in range(warmup):
             step()
-            e1.record(stream)
         torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
-    barrier()
-    step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
-    total_s = max_over_ranks(sum(step_ms) / 1e3, dev)
-    ms_per_step = total_s * 1e3 / args.steps
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(local_rank) as clocks:
+            t0 = time.perf_counter()
+            for e0, e1 in ev:
+                flush.zero_()
+                e0.record(stream)
+                step()
+                e1.record(stream)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+        barrier()
+        step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+        total_s = max_over_ranks(sum(step_ms) / 1e3, dev)
+        v = complex(out.item())
+        return {"total_s": total_s, "mean_s": statistics.mean(step_ms) / 1e3, "wall": wall,
+                "clocks": clocks.summary(), "lhaf": v, "abs_sum": float(asum.item())}
+
     subsets = workmodel.subset_count(N)
-    value = subsets * world * args.steps / total_s
+    tf_run = timed_path(TF, args.steps, args.warmup)
+    fp_run = timed_path(F64, args.steps, args.warmup)
+    ms_per_step = tf_run["total_s"] * 1e3 / args.steps
+    value = subsets * world * args.steps / tf_run["total_s"]
+    tf_instr = workmodel.lhaf_tf_instr(N)
+    tf_ach = tf_instr / tf_run["mean_s"] / 1e12
+    tf_peak = workmodel.FP32_INSTR_PEAK_DERIVED_T
     flops = workmodel.lhaf_flops(N)
-    achieved = flops / (statistics.mean(step_ms) / 1e3) / 1e12
-    peak = workmodel.FP64_PEAK_DERIVED_TFLOPS
-    lhaf_val = complex(out.item())
-    kappa = float(asum.item()) / abs(lhaf_val)
+    sflops = workmodel.survey_flops(N)
+    fp_ach = flops / fp_run["mean_s"] / 1e12
+    fp_peak = workmodel.FP64_PEAK_DERIVED_TFLOPS
+    probes = recorded_probes()
+    fp64 = {"value": subsets * world * args.steps / fp_run["total_s"], "unit": UNIT,
+            "ms_per_step": fp_run["total_s"] * 1e3 / args.steps,
+            "roofline": {"bound": "alu", "achieved": fp_ach, "peak": fp_peak, "unit": "TFLOP/s",
+                         "frac": fp_ach / fp_peak, "traffic": recorded_traffic(N, "fp64"),
+                         "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
+                         "measured_dfma_probe_tflops": probes.get("dfma_tflops"),
+                         "kernel": "lhaf_subsets_kernel<double2>",
+                         "flops_per_launch": flops,
+                         "flops_convention": "the kernel's own algorithm (elimination Hessenberg, "
+                                             "La Budde push form, bordered-matrix loop terms)",
+                         "flops_survey_8d": sflops,
+                         "frac_survey_8d": sflops / fp_run["mean_s"] / 1e12 / fp_peak},
+            "clocks": fp_run["clocks"]}
 
-    # end to end through the public C ABI with host buffers
-    e2e_steps = max(1, min(args.steps, 5))
-    torch.cuda.synchronize()
-    barrier()
-    t = time.perf_counter()
-    for _ in range(e2e_steps):
-        lib.lhaf(A, stream=stream)
-    e2e_s = max_over_ranks(time.perf_counter() - t, dev)
-    e2e = {"value": subsets * world * e2e_steps / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": int(A.nbytes), "d2h_bytes_per_step": 24,
-           "api": "gbsh_lhaf (host matrix in, host result out)"}
+    # end to end through the public C ABI with host buffers (matrix in, value out)
+    def e2e_rate(prec):
+        steps_e = max(1, min(args.steps, 5))
+        torch.cuda.synchronize()
+        barrier()
+        t = time.perf_counter()
+        for _ in range(steps_e):
+            lib.lhaf(A, stream=stream, precision=prec)
+        return subsets * world * steps_e / max_over_ranks(time.perf_counter() - t, dev)
 
-    def large_eval(N, warm):
-        """One timed evaluation of the large single loop hafnian of size N (after a warm-up
-        evaluation if `warm`), CUDA events on the launching stream."""
-        AL = workloads.large_lhaf(N)
+    e2e = {"value": e2e_rate(TF), "unit": UNIT, "h2d_bytes_per_step": int(A.nbytes),
+           "d2h_bytes_per_step": 24, "api": "gbsh_lhaf_ex, GBSH_PREC_TF (host matrix in, "
+                                             "host result out)"}
+    fp64["e2e"] = {"value": e2e_rate(F64), "unit": UNIT, "api": "gbsh_lhaf (FP64)"}
+
+    accuracy = None
+    if ref40 is not None:
+        # the committed fixture matrix (same bits on every host: the generator's QR differs
+        # between LAPACK builds in the last bits), one evaluation per path
+        dR = torch.from_numpy(ref40[0]).to(dev)
+        got = {}
+        for pname, prec in (("tf", TF), ("fp64", F64)):
+            wsR = torch.empty(lib.workspace_size(N, prec), dtype=torch.uint8, device=dev)
+            oR = torch.empty(1, dtype=torch.complex128, device=dev)
+            lib.lhaf_async(dR, oR, wsR, stream=stream, precision=prec)
+            torch.cuda.synchronize()
+            got[pname] = complex(oR.item())
+        accuracy = {"N40": {"matrix": "tests/golden/lhaf_n40.matrix.txt (the N=40 configuration "
+                                      "generator's matrix, seed 0)",
+                            "reference": ref40[2], "tol_stated": 1e-9,
+                            "tf_rel_err": rel_err(got["tf"], ref40[1]),
+                            "fp64_rel_err": rel_err(got["fp64"], ref40[1])}}
+
+    def large_eval(N_, prec, fixture):
+        """One timed evaluation of the large single loop hafnian of size N_ (the kernels are
+        warm from the N=40 steps), CUDA events on the launching stream. The matrix is the
+        committed fixture's where there is one (so that the error against its oracle value
+        can be reported), else the generator's."""
+        g = golden_reference(fixture) if fixture else None
+        AL = g[0] if g is not None else workloads.large_lhaf(N_)
         dL = torch.from_numpy(AL).to(dev)
-        wsL = torch.empty(lib.workspace_size(N), dtype=torch.uint8, device=dev)
+        wsL = torch.empty(lib.workspace_size(N_, prec), dtype=torch.uint8, device=dev)
         oL = torch.empty(1, dtype=torch.complex128, device=dev)
-        if warm:
-            lib.lhaf_async(dL, oL, wsL, stream=stream)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         flush.zero_()
         e0.record(stream)
-        lib.lhaf_async(dL, oL, wsL, stream=stream)
+        lib.lhaf_async(dL, oL, wsL, stream=stream, precision=prec)
         e1.record(stream)
         torch.cuda.synchronize()
         sec = e0.elapsed_time(e1) / 1e3
-        ach = workmodel.lhaf_flops(N) / sec / 1e12
-        return {"workload": f"single loop hafnian N={N} (M={N} Haar U, r=0.8, gamma~CN(0,0.1^2)), "
-                            f"2^{N // 2} subsets, {'1 warm-up + ' if warm else ''}1 timed evaluation",
-                "seconds": sec, "value": workmodel.subset_count(N) / sec, "unit": UNIT,
-                "roofline": {"bound": "alu", "achieved": ach, "peak": peak,
-                             "unit": "TFLOP/s", "frac": ach / peak},
-                "plan": lib.plan(N), "lhaf": [complex(oL.item()).real, complex(oL.item()).imag]}
+        v = complex(oL.item())
+        res = {"seconds": sec, "value": workmodel.subset_count(N_) / sec, "unit": UNIT,
+               "plan": lib.plan(N_, prec), "lhaf": [v.real, v.imag]}
+        if prec == TF:
+            ach = workmodel.lhaf_tf_instr(N_) / sec / 1e12
+            res["roofline"] = {"bound": "alu", "achieved": ach, "peak": tf_peak,
+                               "unit": "T FP32 instr/s", "frac": ach / tf_peak}
+        else:
+            ach = workmodel.lhaf_flops(N_) / sec / 1e12
+            res["roofline"] = {"bound": "alu", "achieved": ach, "peak": fp_peak,
+                               "unit": "TFLOP/s", "frac": ach / fp_peak,
+                               "frac_survey_8d": workmodel.survey_flops(N_) / sec / 1e12 / fp_peak}
+        if g is not None:
+            res["rel_err"] = rel_err(v, g[1])
+            res["reference"] = g[2]
+        return res
 
-    n50 = large_eval(50, True) if (args.n50 and rank == 0) else None
-    n56 = large_eval(56, False) if (args.n56 and rank == 0) else None
+    def large_block(N_, fixture, desc):
+        base = {"workload": f"single loop hafnian N={N_}, {desc}, 2^{N_ // 2} subsets, "
+                            f"1 timed evaluation per path", "matrix": f"tests/golden/{fixture}.matrix.txt",
+                "tol_stated": 1e-7}
+        base["tf"] = large_eval(N_, TF, fixture)
+        base["fp64"] = large_eval(N_, F64, fixture)
+        return base
 
-    def small_latency(A, name, calls=200):
+    n50 = (large_block(50, "lhaf_n50", "M=50 Haar U, r=0.8, gamma~CN(0,0.1^2)")
+           if (args.n50 and rank == 0) else None)
+    n56 = (large_block(56, "lhaf_n56_block", "two 28-mode blocks of the N=56 configuration "
+                                             "(M=28 Haar U, r=0.8, gamma~CN(0,0.1^2)) under a "
+                                             "seeded permutation; reference = product of the "
+                                             "blocks' long-double oracle values")
+           if (args.n56 and rank == 0) else None)
+
+    def small_latency(A_, name, calls=200):
         """Per-call cost of a small evaluation: host wall time of a synchronous gbsh_lhaf with a
         host matrix (copies in and out included), median of `calls`; and device time per
         evaluation of `calls` back-to-back gbsh_lhaf_async on device buffers (CUDA events)."""
-        N = A.shape[0]
-        for _ in range(5):
-            lib.lhaf(A)
-        walls = []
-        for _ in range(calls):
-            t0 = time.perf_counter()
-            lib.lhaf(A)
-            walls.append(time.perf_counter() - t0)
-        dA = torch.from_numpy(A).to(dev)
-        wsS = torch.empty(lib.workspace_size(N), dtype=torch.uint8, device=dev)
-        oS = torch.empty(1, dtype=torch.complex128, device=dev)
-        lib.lhaf_async(dA, oS, wsS, stream=stream)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(calls):
-            lib.lhaf_async(dA, oS, wsS, stream=stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        return {"workload": name, "sync_call_us_median": 1e6 * statistics.median(walls),
-                "device_us_per_eval": 1e3 * e0.elapsed_time(e1) / calls,
-                "kernels_per_eval": lib.plan(N)["kernels"]}
+        N_ = A_.shape[0]
+        res = {"workload": name}
+        for pname, prec in (("fp64", F64), ("tf", TF)):
+            for _ in range(5):
+                lib.lhaf(A_, precision=prec)
+            walls = []
+            for _ in range(calls):
+                t0 = time.perf_counter()
+                lib.lhaf(A_, precision=prec)
+                walls.append(time.perf_counter() - t0)
+            dA_ = torch.from_numpy(A_).to(dev)
+            wsS = torch.empty(lib.workspace_size(N_, prec), dtype=torch.uint8, device=dev)
+            oS = torch.empty(1, dtype=torch.complex128, device=dev)
+            lib.lhaf_async(dA_, oS, wsS, stream=stream, precision=prec)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(calls):
+                lib.lhaf_async(dA_, oS, wsS, stream=stream, precision=prec)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            res[pname] = {"sync_call_us_median": 1e6 * statistics.median(walls),
+                          "device_us_per_eval": 1e3 * e0.elapsed_time(e1) / calls,
+                          "kernels_per_eval": lib.plan(N_, prec)["kernels"]}
+        return res
 
     small = None
     if args.small and rank == 0:
@@ -314,33 +434,38 @@ def run_ours(args, rank, world, local_rank):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, count, dt = time_oracle(A, args.cpu_seconds)
-        cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"{count} random pair subsets of the same N=40 matrix "
-                         f"({dt:.1f} s, plain-C subset formula with explicit matrix powers, "
-                         f"OpenMP over subsets)"}
+        cpu = cpu_baseline_block(A, args.cpu_seconds)
 
     if rank == 0:
+        plan = lib.plan(N, TF)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic (seeded Haar-random GBS kernel matrices)",
+            "dtype": "f32x3", "data": "synthetic (seeded Haar-random GBS kernel matrices)",
             "config": {"workload": WORKLOAD, "N": N, "subsets_per_step_per_gpu": subsets,
+                       "path": "triple-float per subset (GBSH_PREC_TF: three FP32 words, "
+                               "~72-bit significand), compensated FP64 cross-subset sum",
                        "l2": "flushed between timed steps (256 MiB write, outside the events)",
                        "plan": plan, "parallelism": f"replicas x{world}"},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": recorded_traffic(N),
-                         "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
-                         "kernel": "lhaf_subsets_kernel (+expand, finalize in the step time)",
-                         "flops_per_launch": flops},
+            "roofline": {"bound": "alu", "achieved": tf_ach, "peak": tf_peak,
+                         "unit": "T FP32 instr/s", "frac": tf_ach / tf_peak,
+                         "traffic": recorded_traffic(N, "tf"),
+                         "peak_source": "derived: 152 SM x 128 FP32 lanes/clk x 2.07 GHz",
+                         "measured_ffma_probe_t_instr": probes.get("ffma_t_instr"),
+                         "kernel": "lhaf_subsets_kernel<tfc> (+expand, finalize in the step time)",
+                         "work_per_launch": tf_instr,
+                         "work_convention": "FP32 arithmetic instructions of the triple-float "
+                                            "algorithm (216 per complex multiply-add)"},
+            "fp64": fp64,
+            "accuracy": accuracy,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": plan["kernels"] * args.steps,
-            "clocks": clocks.summary(),
-            "wall_s_timed_region": wall,
-            "result": {"lhaf": [lhaf_val.real, lhaf_val.imag], "kappa": kappa,
-                       "err_est": kappa * 2.0 ** -53},
+            "clocks": tf_run["clocks"],
+            "wall_s_timed_region": tf_run["wall"],
+            "result": {"lhaf": [tf_run["lhaf"].real, tf_run["lhaf"].imag],
+                       "kappa": tf_run["abs_sum"] / abs(tf_run["lhaf"])},
             "n50": n50,
             **({"n56": n56} if n56 is not None else {}),
             "small": small,
@@ -352,11 +477,35 @@ def run_ours(args, rank, world, local_rank):
         print(json.dumps(line), flush=True)
 
 
+def cpu_baseline_block(A40, seconds):
+    """The CPU oracle (plain C subset formula, explicit matrix powers, OpenMP over subsets)
+    on the host cores: the configuration workloads N=16 (all 256 subsets), N=40 (a random
+    sample of the step matrix's subsets, the headline comparison) and N=50 (a random sample),
+    each sized to about `seconds`; subset-terms/s per workload and the full-evaluation time
+    they imply."""
+    from paper_2010_15595_gb300 import workloads
+    per = {}
+    for name, A_ in (("N16", workloads.single_lhaf_n16()), ("N40", A40),
+                     ("N50", workloads.large_lhaf(50))):
+        rate, count, dt = time_oracle(A_, seconds if name != "N16" else 1.0)
+        n = (A_.shape[0] + 1) // 2
+        per[name] = {"value": rate, "subsets_timed": count, "seconds": dt,
+                     "full_evaluation_s_implied": (1 << n) / rate}
+    cores = int(os.environ.get("ORACLE_THREADS", "0")) or os.cpu_count()
+    return {"value": per["N40"]["value"], "unit": UNIT, "cores": cores, "kind": "oracle",
+            "cpu_model": host_cpu_model(),
+            "sample": f"{per['N40']['subsets_timed']} random pair subsets of the N=40 step matrix "
+                      f"({per['N40']['seconds']:.1f} s, plain-C subset formula with explicit "
+                      f"matrix powers, OpenMP over subsets); N=16 and N=50 under per_workload",
+            "per_workload": per}
+
+
 def run_batch_workload(lib, workloads, workmodel, dev, stream, count=4096):
     """Batched workload: 4096 loop hafnians of uneven size (N uniform on even 10..30) from
     one M=100-mode state (r=0.7, Haar U, gamma ~ CN(0, 0.1^2)), up to 3 photons per mode,
-    through gbsh_gbs_prob_batch (device B and gamma). FP64, and complex-FP32 per subset
-    with its error against FP64 reported."""
+    through gbsh_gbs_prob_batch (device B and gamma). FP64, triple-float and complex-FP32 per
+    subset. Errors: every FP64 and FP32 result against the triple-float result of the same
+    problem (the triple-float batch is held within 1e-9 of the oracle by the tests)."""
     import numpy as np
     import torch
     B, gamma = workloads.batch_state()
@@ -366,11 +515,12 @@ def run_batch_workload(lib, workloads, workmodel, dev, stream, count=4096):
     dg = torch.from_numpy(gamma).to(dev)
     subsets = int(sum(workmodel.subset_count(int(n)) for n in Ns))
     flops = float(sum(workmodel.lhaf_flops(int(n)) for n in Ns))
+    tfi = float(sum(workmodel.lhaf_tf_instr(int(n)) for n in Ns))
     res = {"workload": f"{count} loop hafnians, N uniform on even 10..30, M=100 Haar state "
                        "r=0.7, gamma~CN(0,0.1^2), <=3 photons/mode (gbsh_gbs_prob_batch, "
                        "host result copy included)", "subset_terms": subsets}
     out = {}
-    for name, prec in (("fp64", lib.PREC_FP64), ("c32", lib.PREC_C32)):
+    for name, prec in (("fp64", lib.PREC_FP64), ("tf", lib.PREC_TF), ("c32", lib.PREC_C32)):
         lib.gbs_prob_batch(dB, dg, pats, precision=prec, stream=stream)
         torch.cuda.synchronize()
         t = time.perf_counter()
@@ -384,10 +534,14 @@ def run_batch_workload(lib, workloads, workmodel, dev, stream, count=4096):
     res["fp64"]["roofline"] = {"bound": "alu", "achieved": ach,
                                "peak": workmodel.FP64_PEAK_DERIVED_TFLOPS, "unit": "TFLOP/s",
                                "frac": ach / workmodel.FP64_PEAK_DERIVED_TFLOPS}
-    err = np.abs(out["c32"] - out["fp64"]) / np.abs(out["fp64"])
-    res["c32"]["rel_err_vs_fp64"] = {"median": float(np.median(err)),
-                                     "p99": float(np.quantile(err, 0.99)),
-                                     "max": float(err.max())}
+    ach = tfi / res["tf"]["seconds"] / 1e12
+    res["tf"]["roofline"] = {"bound": "alu", "achieved": ach,
+                             "peak": workmodel.FP32_INSTR_PEAK_DERIVED_T, "unit": "T FP32 instr/s",
+                             "frac": ach / workmodel.FP32_INSTR_PEAK_DERIVED_T}
+    for name in ("fp64", "c32"):
+        err = np.abs(out[name] - out["tf"]) / np.abs(out["tf"])
+        res[name]["rel_err_vs_tf"] = {"median": float(np.median(err)),
+                                      "p99": float(np.quantile(err, 0.99)), "max": float(err.max())}
     res["c32"]["enabled_by_mixed_mode_for_N_le"] = lib.C32_MAX_N
     return res
 
@@ -396,9 +550,10 @@ def run_serving_workload(args):
     """Chain-rule sampler (Sec. III) on the serving state: M=100 modes, Haar U, r=0.8 on 25
     input modes (mean ~20 photons), output displacement ~CN(0, 0.1^2), Fock cutoff 4, loop
     hafnians up to N=36. Plain path (one single-evaluation launch sequence and one
-    synchronisation per loop hafnian, one sample at a time) vs
-    the served path (continuous batching); Poisson arrivals at fixed multiples of the plain
-    throughput; latencies from submission to completion."""
+    synchronisation per loop hafnian, one sample at a time) vs the served path (continuous
+    batching); Poisson arrivals at 0.5, 1, 2 and 3 times the plain throughput; latencies from
+    submission to completion, with n per rate; the fraction of samples that dropped a
+    candidate above the N <= 36 cap."""
     import numpy as np
     from paper_2010_15595_gb300 import sampler as S, workloads
     U, r, alpha = workloads.serving_state()
@@ -409,25 +564,29 @@ def run_serving_workload(args):
     def run_batch(smp, seeds):
         t = time.perf_counter()
         rids = [smp.submit(s_) for s_ in seeds]
-        out = [smp.wait(rr, timeout=900) for rr in rids]
+        out = [smp.wait(rr, timeout=1800) for rr in rids]
         return time.perf_counter() - t, out
 
     with S.Sampler(st, cutoff=4, n_cap=36, batching=False) as plain:
         dt, out = run_batch(plain, range(args.serve_plain))
     plain_rate = args.serve_plain / dt
-    lat = [o[1]["latency_s"] for o in out]
+    lat = np.array([o[1]["latency_s"] for o in out])
     res["plain"] = {"samples": args.serve_plain, "samples_per_s": plain_rate,
                     "mean_photons": float(np.mean([o[0].sum() for o in out])),
-                    "note": "all submitted at t=0 (saturated)"}
+                    "per_sample_s_p50": float(np.median(np.diff(np.sort(lat), prepend=0.0))),
+                    "note": "all submitted at t=0 (saturated), served one at a time"}
     with S.Sampler(st, cutoff=4, n_cap=36, max_active=args.serve_slots) as smp:
         dt, out = run_batch(smp, range(1000, 1000 + args.serve_saturated))
+        capped = sum(1 for o in out if o[1]["truncated"] > 0)
         res["served_saturated"] = {"samples": args.serve_saturated,
                                    "samples_per_s": args.serve_saturated / dt,
                                    "truncated_steps": int(sum(o[1]["truncated"] for o in out)),
+                                   "samples_with_capped_candidate": capped,
+                                   "capped_fraction": capped / args.serve_saturated,
                                    "slots": args.serve_slots}
         rng = np.random.default_rng(2)
         res["poisson"] = []
-        for mult in (0.5, 0.8, 1.0):
+        for mult in args.serve_rates:
             lam = mult * plain_rate
             gaps = rng.exponential(1.0 / lam, args.serve_poisson)
             t0 = time.perf_counter()
@@ -437,14 +596,32 @@ def run_serving_workload(args):
                 now = time.perf_counter()
                 if target > now:
                     time.sleep(target - now)
-                rids.append(smp.submit(5000 + 100 * int(mult * 10) + i))
-            outs = [smp.wait(rr, timeout=900) for rr in rids]
+                rids.append(smp.submit(5000 + 1000 * int(mult * 10) + i))
+            outs = [smp.wait(rr, timeout=1800) for rr in rids]
             span = time.perf_counter() - t0
             lats = np.array([o[1]["latency_s"] for o in outs])
             res["poisson"].append({"rate_x_plain": mult, "arrival_per_s": lam,
                                    "requests": len(outs), "samples_per_s": len(outs) / span,
                                    "p50_s": float(np.median(lats)),
-                                   "p99_s": float(np.quantile(lats, 0.99))})
+                                   "p99_s": float(np.quantile(lats, 0.99)),
+                                   "max_s": float(lats.max())})
+    # the plain path under the same arrivals: a queue in front of a single server
+    res["plain_queue_model"] = []
+    for mult in args.serve_rates:
+        lam = mult * plain_rate
+        gaps = np.random.default_rng(2).exponential(1.0 / lam, args.serve_poisson)
+        svc = np.random.default_rng(3).choice(np.diff(np.sort(lat), prepend=0.0), args.serve_poisson)
+        arr = np.cumsum(gaps)
+        done = np.zeros_like(arr)
+        free = 0.0
+        for i in range(len(arr)):
+            start = max(arr[i], free)
+            free = done[i] = start + svc[i]
+        wl = done - arr
+        res["plain_queue_model"].append({"rate_x_plain": mult, "p50_s": float(np.median(wl)),
+                                         "p99_s": float(np.quantile(wl, 0.99)),
+                                         "note": "FIFO single server with the measured plain "
+                                                 "per-sample service times (not run)"})
     res["served_vs_plain_samples_per_s"] = res["served_saturated"]["samples_per_s"] / plain_rate
     return res
 
@@ -500,7 +677,8 @@ def telephone(n: int) -> int:
 
 def fig2_allones(sizes_fp64=range(30, 58, 2), sizes_dd=range(30, 48, 2)):
     """Sec. IV, Fig. 2: relative error of lhaf(all-ones n x n) against T(n), with the FP64
-    kernels (gbsh_lhaf) and the double-double per-subset variant (batched entry point)."""
+    kernels (gbsh_lhaf), the triple-float path (gbsh_lhaf_ex, every size) and the
+    double-double per-subset variant (batched entry point, sizes_dd)."""
     from fractions import Fraction
     import numpy as np
     from paper_2010_15595_gb300 import lib
@@ -516,6 +694,10 @@ def fig2_allones(sizes_fp64=range(30, 58, 2), sizes_dd=range(30, 48, 2)):
         v = lib.lhaf(A)
         dt = time.perf_counter() - t
         row = {"n": n, "fp64_rel_err": rel(v, n)[0], "fp64_seconds": dt}
+        t = time.perf_counter()
+        vt = lib.lhaf(A, precision=lib.PREC_TF)
+        row["tf_rel_err"] = rel(vt, n)[0]
+        row["tf_seconds"] = time.perf_counter() - t
         if n in sizes_dd:
             t = time.perf_counter()
             vd = lib.lhaf_batch([A], precision=lib.PREC_DD)[0]
@@ -572,10 +754,12 @@ def main(argv=None):
                    help="also time one N=56 evaluation (2^28 subsets, about a minute)")
     p.add_argument("--no-batch", dest="batch", action="store_false")
     p.add_argument("--no-serving", dest="serving", action="store_false")
-    p.add_argument("--serve-plain", type=int, default=6)
-    p.add_argument("--serve-saturated", type=int, default=192)
+    p.add_argument("--serve-plain", type=int, default=50)
+    p.add_argument("--serve-saturated", type=int, default=256)
     p.add_argument("--serve-slots", type=int, default=256)
-    p.add_argument("--serve-poisson", type=int, default=16)
+    p.add_argument("--serve-poisson", type=int, default=60,
+                   help="requests per arrival rate (the committed serving profile uses 200)")
+    p.add_argument("--serve-rates", type=float, nargs="+", default=[0.5, 1.0, 2.0, 3.0])
     p.add_argument("--fig1", action="store_true",
                    help="run the Fig. 1 TVD experiment (Sec. III) instead of the benchmark")
     p.add_argument("--fig1-samples", type=int, default=200000)

@@ -312,6 +312,20 @@ template <> __device__ __forceinline__ tf3 inv_int<tf3>(int k) {
   return tf3(c_inv_tf[k][0], c_inv_tf[k][1], c_inv_tf[k][2]);
 }
 
+// for (i = begin; i < end; i += step) f(i), kept rolled on the triple-float path: a
+// triple-float complex multiply-accumulate is ~220 FP32 instructions, and unrolled copies
+// of loops made of them overflow the instruction cache (the profile showed warps stalled
+// on instruction fetch). The other arithmetic types get the plain loop.
+template <class T, class F>
+__device__ __forceinline__ void for_rolled(int begin, int end, int step, F&& f) {
+  if constexpr (std::is_same<T, tfc>::value) {
+#pragma unroll 1
+    for (int i = begin; i < end; i += step) f(i);
+  } else {
+    for (int i = begin; i < end; i += step) f(i);
+  }
+}
+
 // Compensated (two-sum) accumulator for the signed subset sum.
 struct DDAcc {
   double re_hi, re_lo, im_hi, im_lo, abs_sum;
@@ -359,7 +373,7 @@ __device__ __forceinline__ void column_update(T* __restrict__ H, int ldh, int S,
   if (!seg) {
     for (int r = lane; r < S; r += 32) {
       T acc = zero;
-      for (int i = c + 2; i < S; ++i) acc = cfma(acc, H[r * ldh + i], H[i * ldh + c]);
+      for_rolled<T>(c + 2, S, 1, [&](int i) { acc = cfma(acc, H[r * ldh + i], H[i * ldh + c]); });
       H[r * ldh + c + 1] = cfma(acc, r == c + 1 ? one : piv, H[r * ldh + c + 1]);
     }
     return;
@@ -375,7 +389,7 @@ __device__ __forceinline__ void column_update(T* __restrict__ H, int ldh, int S,
   int i = o;
   const int cnt = e1 - e0;
   const T* xr = H + ra * ldh + c + 2;
-  for (int t = 0; t < q; ++t) {
+  for_rolled<T>(0, q, 1, [&](int t) {
     if (t < cnt) {
       acc = cfma(acc, xr[i], H[(c + 2 + i) * ldh + c]);
       if (++i == Rr) {
@@ -386,7 +400,7 @@ __device__ __forceinline__ void column_update(T* __restrict__ H, int ldh, int S,
         acc = zero;
       }
     }
-  }
+  });
   const T a0 = nfl >= 1 ? h0 : acc;
   const T a1 = nfl >= 2 ? h1 : (nfl == 1 ? acc : zero);
   const T a2 = nfl >= 2 ? acc : zero;
@@ -546,12 +560,12 @@ __device__ __noinline__ Term subset_term_full(const Problem& P, uint64_t z, int 
       // rows r >= c+2:  H[r][j] -= m_r u_j,  j >= c+1
       {
         const int C = Rr + 1;
-        for (int e = lane; e < Rr * C; e += 32) {
+        for_rolled<T>(lane, Rr * C, 32, [&](int e) {
           int rr = e / C, jj = e - rr * C;
           int r = c + 2 + rr, j = c + 1 + jj;
           const T u = H[(c + 1) * ldh + (jj == 0 ? c : j)];
           H[r * ldh + j] = cfms(H[r * ldh + j], H[r * ldh + c], u);
-        }
+        });
       }
       __syncwarp();
     }
@@ -617,7 +631,7 @@ __device__ __noinline__ Term subset_term_full(const Problem& P, uint64_t z, int 
     {
       const int nt = S - s;                            // targets t = s+1 .. S
       const int ne = (degs < D - 1 ? degs : D - 1) + 1;
-      for (int f = lane; f < nt * ne; f += 32) {
+      for_rolled<T>(lane, nt * ne, 32, [&](int f) {
         const int ti = f / ne, e = f - ti * ne;
         const int t = s + 1 + ti;
         const int d = e + 1 + ti;
@@ -627,7 +641,7 @@ __device__ __noinline__ Term subset_term_full(const Problem& P, uint64_t z, int 
           T* Pt = Pl + poly_offset(t, D);
           Pt[d] = cfms(Pt[d], H[a * ldh + bcol], Ps[e]);
         }
-      }
+      });
     }
     __syncwarp();
     {

@@ -392,7 +392,9 @@ bool make_plan(int N, const DeviceInfo& dev, int warps_main, int kcap_override, 
       if ((size_t)W * area_bytes(k) <= limit) kc = k;
     return kc;
   };
-  int W = warps_main > 0 ? warps_main : 12;
+  // default cap: 12 warps per CTA for FP64 (the FP64 pipe is the limit, measured best);
+  // 16 for triple-float, whose FP32 instruction stream needs more warps to hide latency
+  int W = warps_main > 0 ? warps_main : (prec == kPrecTF ? 16 : 12);
   if (W > kMaxWarps) W = kMaxWarps;
   // Popcount classes: subsets with popcount in (k_prev, k_c] run in one launch with W_c warps
   // per CTA, W_c the largest count of a fixed ladder (capped at W) whose work areas fit.

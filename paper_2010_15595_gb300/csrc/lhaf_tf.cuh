@@ -182,14 +182,16 @@ struct tfc {
 };
 
 __device__ __forceinline__ tfc cadd(tfc p, tfc q) { return tfc{p.x + q.x, p.y + q.y}; }
-// acc + p*q
-__device__ __forceinline__ tfc cfma(tfc acc, tfc p, tfc q) {
-  return tfc{tf_dot2(p.x, q.x, -p.y, q.y, acc.x), tf_dot2(p.x, q.y, p.y, q.x, acc.y)};
-}
+// The complex multiply-accumulates are ~220 FP32 instructions each and appear at many
+// places of the per-subset code; compiled out of line, one copy serves every call site, so
+// the instruction footprint of the hot loops stays inside the instruction cache (inlined,
+// the warps spent most of their time waiting for instructions: 1.4x slower at N = 40).
 // acc - p*q
-__device__ __forceinline__ tfc cfms(tfc acc, tfc p, tfc q) {
+__device__ __noinline__ tfc cfms(tfc acc, tfc p, tfc q) {
   return tfc{tf_dot2(-p.x, q.x, p.y, q.y, acc.x), tf_dot2(-p.x, q.y, -p.y, q.x, acc.y)};
 }
+// acc + p*q, through the same out-of-line code
+__device__ __forceinline__ tfc cfma(tfc acc, tfc p, tfc q) { return cfms(acc, tfc{-p.x, -p.y}, q); }
 __device__ __forceinline__ tfc cmul(tfc p, tfc q) {
   const tf3 z(0.0f);
   return cfma(tfc{z, z}, p, q);
