@@ -176,11 +176,16 @@ def mu_from_alpha(alpha):
 
 # ------------------------------------------------------------ chain rule (Sec. III)
 
-def chain_rule_sample(V, R, cutoff: int, normals: np.ndarray, uniforms: np.ndarray):
+def chain_rule_sample(V, R, cutoff: int, normals: np.ndarray, uniforms: np.ndarray,
+                      threshold: bool = False):
     """One sample of the algorithm of Sec. III for a pure state (steps 2-6), with the random
     numbers passed in: `normals` (2(m-1) standard normals for the heterodyne draw of modes
     2..m) and `uniforms` (m numbers in [0, 1) for the draws of s_1..s_m). Conditioning uses
-    Eqs. condV/condR at every step. Returns (pattern, per-step probability vectors)."""
+    Eqs. condV/condR at every step. Returns (pattern, per-step probability vectors).
+    threshold=True returns the threshold-detector outcome instead of the photon numbers:
+    a detector clicks (1) when its mode holds one photon or more (end of Sec. III: threshold
+    samples are photon-number samples with every nonzero count replaced by 1); the
+    probability vectors are those of the photon-number chain."""
     m = V.shape[0] // 2
     rest = list(range(1, m))
     mu = np.zeros(0)
@@ -207,4 +212,6 @@ def chain_rule_sample(V, R, cutoff: int, normals: np.ndarray, uniforms: np.ndarr
         cdf = np.cumsum(p / p.sum())
         sk = int(np.searchsorted(cdf, uniforms[k - 1], side="right"))
         s.append(min(sk, cutoff))
+    if threshold:
+        return [1 if x > 0 else 0 for x in s], probs
     return s, probs

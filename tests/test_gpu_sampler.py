@@ -39,6 +39,28 @@ def test_matches_oracle_chain_rule_with_same_randoms():
         assert list(g[0]) == ref, (seed, g[0], ref)
 
 
+def test_threshold_matches_oracle_with_same_randoms():
+    """Threshold detectors (end of Sec. III): the GPU sampler configured for clicks against
+    the oracle's chain-rule sampler with threshold output, driven by the same Philox
+    stream (the oracle conditions by Eqs. condV/condR at every step)."""
+    from paper_2010_15595_gb300 import sampler as S
+    U, rv, al = _phys(4, 5, r=0.8)
+    m, cutoff = 4, 4
+    st = S.pure_state(U, rv, al)
+    V, R = G.pure_state_covariance(U, rv), G.means_from_alpha(al)
+    seeds = list(range(300, 316))
+    with S.Sampler(st, cutoff=cutoff, n_cap=60, max_active=64, threshold=True) as smp:
+        got = _run(smp, seeds)
+    clicks_seen = 0
+    for seed, g in zip(seeds, got):
+        z = OP.chain_normals(seed, 0, 2 * (m - 1))
+        u = OP.chain_uniforms(seed, 0, m)
+        ref, _ = G.chain_rule_sample(V, R, cutoff, z, u, threshold=True)
+        assert list(g[0]) == ref, (seed, g[0], ref)
+        clicks_seen += sum(ref)
+    assert clicks_seen > 0
+
+
 def test_same_alone_and_in_mix_and_plain():
     from paper_2010_15595_gb300 import sampler as S
     U, rv, al = _phys(6, 2, r=0.7)

@@ -277,3 +277,63 @@ def test_mixed_form_thermal_closed_form():
     for n in range(6):
         assert G.prob_mixed(q["A"], q["gamma"], q["pvac"], [n]) == pytest.approx(
             nbar ** n / (nbar + 1) ** (n + 1), rel=1e-12)
+
+
+# ---------------------------------------------------------------- long-double oracle
+
+@pytest.mark.parametrize("n", [24, 26, 28])
+def test_long_double_more_accurate_all_ones(n):
+    """The long-double subset formula (the reference of every stated-tolerance gate at
+    N >= 32) carries more precision than the double one: against the exact T(n), its error
+    is at least 100x smaller (11 more significand bits, ~2000x nominally)."""
+    from fractions import Fraction
+    A = W.all_ones(n)
+    T = telephone(n)
+    err_d = float(abs(Fraction(L.lhaf_subset(A).real) - T) / T)
+    err_ld = float(abs(Fraction(L.lhaf_subset_ld(A).real) - T) / T)
+    assert err_d > 0
+    assert 100 * err_ld <= err_d, (n, err_d, err_ld)
+
+
+@pytest.mark.parametrize("n", [12, 14])
+def test_long_double_more_accurate_double_factorial(n):
+    """haf(all-ones 2n) = (2n-1)!! through the long-double formula, 100x closer than double."""
+    from fractions import Fraction
+    A = W.all_ones(2 * n)
+    np.fill_diagonal(A, 0)
+    df = double_factorial_odd(n)
+    err_d = float(abs(Fraction(L.lhaf_subset(A).real) - df) / df)
+    err_ld = float(abs(Fraction(L.lhaf_subset_ld(A).real) - df) / df)
+    assert err_d > 0
+    assert 100 * err_ld <= err_d, (n, err_d, err_ld)
+
+
+# ---------------------------------------------------------------- Eq. GBS (zero displacement)
+
+def test_zero_displacement_formula_single_mode():
+    """Eq. GBS, p(S) = haf(A_S) / (sqrt(det Q) prod s_i!), on squeezed vacuum equals the
+    closed form p(2n) = tanh^{2n} r (2n)! / (2^n n!)^2 / cosh r, and 0 for odd counts."""
+    import math as _m
+    from oracle import gbs as G
+    r = 0.55
+    q = G.gbs_quantities(G.pure_state_covariance(np.eye(1, dtype=complex), np.array([r])),
+                         np.zeros(2))
+    for n in range(9):
+        want = 0 if n % 2 else np.tanh(r) ** n * _m.factorial(n) / (2 ** (n // 2) * _m.factorial(n // 2)) ** 2 / np.cosh(r)
+        assert G.prob_zero_displacement(q["A"], q["Q"], [n]) == pytest.approx(want, abs=1e-15)
+
+
+def test_zero_displacement_formula_equals_loop_form_mixed():
+    """On a lossy (mixed) 3-mode state with zero displacement, Eq. GBS equals Eq. lhaf
+    (whose fill vector is then zero, so the loop hafnian is the hafnian)."""
+    from oracle import gbs as G
+    rng = W.rng_for(93, 0)
+    U = W.haar_unitary(3, rng)
+    V = G.pure_state_covariance(U, np.array([0.6, 0.4, 0.3]))
+    eta = 0.7  # loss channel: V -> eta V + (1 - eta) hbar/2 I
+    V = eta * V + (1 - eta) * (G.HBAR / 2) * np.eye(6)
+    q = G.gbs_quantities(V, np.zeros(6))
+    assert np.allclose(q["gamma"], 0)
+    for S in [(0, 0, 0), (1, 1, 0), (2, 0, 0), (1, 2, 1), (2, 2, 2)]:
+        assert G.prob_zero_displacement(q["A"], q["Q"], S) == pytest.approx(
+            G.prob_mixed(q["A"], q["gamma"], q["pvac"], S), rel=1e-12, abs=1e-18)

@@ -122,3 +122,21 @@ def test_mixed_builder_reduces_to_pure_builder():
     assert np.abs(mx.fill_map @ mx.mean - pu.gamma).max() < 1e-10
     assert np.abs(mx.B - pu.B).max() < 1e-10
     assert np.abs(mx.het_chol - pu.het_chol).max() < 1e-8
+
+
+def test_oracle_threshold_output_is_clicks_of_photon_sample():
+    """The oracle's threshold output is min(s_i, 1) of the photon-number sample drawn from
+    the same random numbers."""
+    import numpy as np
+    from oracle import gbs as G
+    from paper_2010_15595_gb300 import workloads as W
+    rng = W.rng_for(94, 0)
+    U = W.haar_unitary(3, rng)
+    V = G.pure_state_covariance(U, np.array([0.9, 0.7, 0.5]))
+    R = G.means_from_alpha(W.complex_normal(3, 0.3, rng))
+    r2 = np.random.default_rng(5)
+    for _ in range(10):
+        z, u = r2.standard_normal(4), r2.random(3)
+        s, _ = G.chain_rule_sample(V, R, 5, z, u)
+        t, _ = G.chain_rule_sample(V, R, 5, z, u, threshold=True)
+        assert t == [min(x, 1) for x in s]
