@@ -219,6 +219,33 @@ int gbsh_gbs_prob(const gbsh_c128* B, int M, int ldb, const gbsh_c128* gamma,
                   void* stream);
 
 /*
+ * gbsh_lhaf_range_async — the part of the subset sum (Sec. II after Eq. lhaf-pure: the
+ * signed sum over the 2^n subsets Z of index pairs) that comes from the subsets
+ * z = i XOR (i >> 1) for enumeration indices i in [i_begin, i_end), n = ceil(N/2). Any
+ * partition of [0, 2^n) into ranges covers every subset exactly once, so ranges can be
+ * evaluated separately -- on different GPUs, in different processes -- and combined with
+ * gbsh_combine_partials: the only exchange a split of one loop hafnian needs.
+ *   dA, N, lda, precision, workspace, stream: as for gbsh_lhaf_async_ex (the workspace must
+ *               hold gbsh_lhaf_workspace_size_ex(N, precision) bytes).
+ *   d_partial   device array of 5 doubles, receives the range's compensated partial
+ *               (re_hi, re_lo, im_hi, im_lo, sum |Re p_Z| + |Im p_Z|): the sum over the
+ *               range is (re_hi + re_lo) + i (im_hi + im_lo).
+ * The range is cut into chunks of the size gbsh_lhaf uses for N, starting at i_begin.
+ * No synchronisation. Errors: GBSH_EINVAL (sizes, i_begin > i_end, i_end > 2^n, null
+ * pointers, unsupported precision), GBSH_ECUDA.
+ */
+int gbsh_lhaf_range_async(const gbsh_c128* dA, int N, int lda, int precision, uint64_t i_begin,
+                          uint64_t i_end, double* d_partial, void* workspace,
+                          size_t workspace_bytes, void* stream);
+
+/*
+ * gbsh_combine_partials — host-side sum of `count` range partials (host array, count x 5
+ * doubles as written by gbsh_lhaf_range_async) into out[5], compensated (TwoSum on the high
+ * words, low words added), in the given order. Host code only: no device, no allocation.
+ */
+int gbsh_combine_partials(const double* partials, int count, double* out);
+
+/*
  * gbsh_subset_terms — diagnostic: the individual subset terms p_Z (before the sign
  * (-1)^{n-|Z|}) of the subset sum for the listed subsets z of the pairs (j, j+n) of A
  * padded to even size Ne = N + (N odd), n = Ne/2; bit j of z <=> pair j in Z.

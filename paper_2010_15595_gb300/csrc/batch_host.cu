@@ -48,26 +48,32 @@ std::atomic<bool> g_graphs_enabled{true};
 std::atomic<long long> g_captures{0}, g_replays{0};
 cudaStream_t g_cap_stream[64] = {}, g_cap_side[64] = {};
 
-// Returns the exec for `key` (nullptr if none yet); records first sightings.
-cudaGraphExec_t graph_lookup(const GraphKey& key, bool* capture_now) {
+// If an executable graph for `key` is cached, launches it on `st` while holding the cache
+// lock (so that another thread's eviction cannot destroy it between lookup and launch) and
+// returns true with the launch status in *e. Otherwise records the first sighting of the
+// key, or sets *capture_now on its second one, and returns false.
+bool graph_try_launch(const GraphKey& key, cudaStream_t st, bool* capture_now, cudaError_t* e) {
   std::lock_guard<std::mutex> lk(g_graph_mu);
   *capture_now = false;
   for (GraphEntry& g : g_graphs)
     if (g.key == key) {
       g.last_use = ++g_clock;
-      return g.exec;
+      *e = cudaGraphLaunch(g.exec, st);
+      return true;
     }
   for (const GraphKey& k : g_seen)
     if (k == key) {
       *capture_now = true;
-      return nullptr;
+      return false;
     }
   if (g_seen.size() >= kMaxSeenKeys) g_seen.erase(g_seen.begin());
   g_seen.push_back(key);
-  return nullptr;
+  return false;
 }
 
-void graph_store(const GraphKey& key, cudaGraphExec_t exec) {
+// Caches a newly captured graph (evicting the least recently used one; an evicted graph
+// still in flight is freed by CUDA when it completes) and launches it under the lock.
+cudaError_t graph_store_and_launch(const GraphKey& key, cudaGraphExec_t exec, cudaStream_t st) {
   std::lock_guard<std::mutex> lk(g_graph_mu);
   if (g_graphs.size() >= kMaxGraphs) {
     auto lru = std::min_element(g_graphs.begin(), g_graphs.end(),
@@ -78,6 +84,7 @@ void graph_store(const GraphKey& key, cudaGraphExec_t exec) {
     g_graphs.erase(lru);
   }
   g_graphs.push_back(GraphEntry{key, exec, ++g_clock});
+  return cudaGraphLaunch(exec, st);
 }
 
 // Captures launch_batch for `key` into an executable graph (nullptr on any failure: the
@@ -197,7 +204,7 @@ cudaError_t batch_run(BatchLayout& L, const std::vector<BatchInput>& in, int cou
   if (e != cudaSuccess) return e;
   const int W = batch_warps_for(std::max(L.n_max, 1), precision, dev, warps_pref);
   if (W < 1) return cudaErrorInvalidValue;
-  cudaGraphExec_t exec = nullptr;
+  bool launched = false;
   if (g_graphs_enabled.load() && count > 0) {
     int d = 0;
     e = cudaGetDevice(&d);
@@ -205,16 +212,17 @@ cudaError_t batch_run(BatchLayout& L, const std::vector<BatchInput>& in, int cou
     const GraphKey key{d, count, L.n_max, precision, W, L.total_chunks, w + L.off_in,
                        w + L.off_prob, w + L.off_counter, w + L.off_partials, w + L.off_out};
     bool capture_now = false;
-    exec = graph_lookup(key, &capture_now);
-    if (!exec && capture_now) {
-      exec = graph_capture(key, L, w, count, precision, W);
-      if (exec) graph_store(key, exec);
+    launched = graph_try_launch(key, st, &capture_now, &e);
+    if (!launched && capture_now) {
+      cudaGraphExec_t exec = graph_capture(key, L, w, count, precision, W);
+      if (exec) {
+        e = graph_store_and_launch(key, exec, st);
+        launched = true;
+      }
     }
+    if (launched && e == cudaSuccess) g_replays.fetch_add(1);
   }
-  if (exec) {
-    e = cudaGraphLaunch(exec, st);
-    if (e == cudaSuccess) g_replays.fetch_add(1);
-  } else {
+  if (!launched) {
     e = launch_batch(reinterpret_cast<const BatchInput*>(w + L.off_in),
                      reinterpret_cast<const BatchProblem*>(w + L.off_prob), count, L.total_chunks,
                      L.n_max, precision, W, reinterpret_cast<unsigned*>(w + L.off_counter),

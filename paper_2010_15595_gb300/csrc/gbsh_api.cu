@@ -319,6 +319,45 @@ int gbsh_lhaf_async_ex(const gbsh_c128* dA, int N, int lda, int precision, gbsh_
   return GBSH_OK;
 }
 
+int gbsh_lhaf_range_async(const gbsh_c128* dA, int N, int lda, int precision, uint64_t i_begin,
+                          uint64_t i_end, double* d_partial, void* workspace,
+                          size_t workspace_bytes, void* stream) {
+  if (N < 1 || N > GBSH_MAX_N || !dA || lda < N || !d_partial || !workspace) return GBSH_EINVAL;
+  if (!valid_single_precision(precision)) return GBSH_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(workspace) & 255u) != 0) return GBSH_EINVAL;
+  const int n = (N + (N & 1)) / 2;
+  if (i_begin > i_end || i_end > ((uint64_t)1 << n)) return GBSH_EINVAL;
+  gbsh::LhafPlan plan;
+  int rc = plan_for(N, &plan, precision);
+  if (rc != GBSH_OK) return rc;
+  if (workspace_bytes < plan.bytes) return GBSH_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  GBSH_CUDA(gbsh::launch_lhaf_range(plan, reinterpret_cast<const double2*>(dA), lda, workspace,
+                                    st, i_begin, i_end));
+  const char* res = static_cast<const char*>(workspace) + plan.off_out + 3 * sizeof(double);
+  GBSH_CUDA(cudaMemcpyAsync(d_partial, res, 5 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  return GBSH_OK;
+}
+
+int gbsh_combine_partials(const double* partials, int count, double* out) {
+  if (count < 0 || !out || (count > 0 && !partials)) return GBSH_EINVAL;
+  double re_hi = 0, re_lo = 0, im_hi = 0, im_lo = 0, as = 0;
+  auto two_sum = [](double a, double b, double& s, double& e) {
+    s = a + b;
+    const double bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+  };
+  for (int q = 0; q < count; ++q) {  // fixed input order
+    const double* p = partials + 5 * (size_t)q;
+    double s, e;
+    two_sum(re_hi, p[0], s, e); re_hi = s; re_lo += e + p[1];
+    two_sum(im_hi, p[2], s, e); im_hi = s; im_lo += e + p[3];
+    as += p[4];
+  }
+  out[0] = re_hi; out[1] = re_lo; out[2] = im_hi; out[3] = im_lo; out[4] = as;
+  return GBSH_OK;
+}
+
 int gbsh_gbs_prob(const gbsh_c128* B, int M, int ldb, const gbsh_c128* gamma,
                   const int* pattern, double p_vac, double* prob, gbsh_c128* lhaf_out,
                   void* stream) {

@@ -53,8 +53,9 @@ __global__ void expand_problem_kernel(const double2* __restrict__ base, int ld,
 template <class T, bool kVisit>
 __global__ void __launch_bounds__(32 * kMaxWarps, 1)
 lhaf_subsets_kernel(Problem P, int k_lo, int k_hi, int area_elems, uint64_t chunk_size,
-                    unsigned nchunks, unsigned* __restrict__ counter,
-                    double* __restrict__ partials, unsigned* __restrict__ visits) {
+                    uint64_t i_base, uint64_t i_end, unsigned nchunks,
+                    unsigned* __restrict__ counter, double* __restrict__ partials,
+                    unsigned* __restrict__ visits) {
   extern __shared__ double2 smem_raw[];
   T* smem = reinterpret_cast<T*>(smem_raw);
   const int lane = threadIdx.x & 31;
@@ -69,7 +70,9 @@ lhaf_subsets_kernel(Problem P, int k_lo, int k_hi, int area_elems, uint64_t chun
     if (ch >= nchunks) break;
     DDAcc acc;
     acc.zero();
-    const uint64_t i0 = (uint64_t)ch * chunk_size, i1 = i0 + chunk_size;
+    // chunk ch covers the enumeration indices [i0, i1) of the evaluated range
+    const uint64_t i0 = i_base + (uint64_t)ch * chunk_size;
+    const uint64_t i1 = i0 + chunk_size < i_end ? i0 + chunk_size : i_end;
     for (uint64_t i = i0; i < i1; ++i) {
       const uint64_t z = i ^ (i >> 1);  // Gray-code order of the chunk's indices
       const int k = __popcll(z);
@@ -140,8 +143,8 @@ __device__ __forceinline__ void block_tree(DDAcc a, double (*sh)[kFinalizeThread
 }
 
 __global__ void __launch_bounds__(kFinalizeThreads)
-lhaf_partials_kernel(const double* __restrict__ partials, unsigned nchunks, int nclass,
-                     double* __restrict__ block_out) {
+lhaf_partials_kernel(const double* __restrict__ partials, unsigned nchunks, unsigned stride,
+                     int nclass, double* __restrict__ block_out) {
   __shared__ double sh[5][kFinalizeThreads];
   const unsigned per = (nchunks + gridDim.x - 1) / gridDim.x;
   const unsigned c0 = blockIdx.x * per;
@@ -149,7 +152,7 @@ lhaf_partials_kernel(const double* __restrict__ partials, unsigned nchunks, int 
   DDAcc a;
   a.zero();
   for (int cls = 0; cls < nclass; ++cls) {
-    const double* p = partials + (size_t)cls * nchunks * 5;
+    const double* p = partials + (size_t)cls * stride * 5;
     for (unsigned ch = c0 + threadIdx.x; ch < c1; ch += kFinalizeThreads) add_partial(a, p + (size_t)ch * 5);
   }
   block_tree(a, sh);
@@ -168,6 +171,8 @@ lhaf_finalize_kernel(const double* __restrict__ block_out, int nblocks, double* 
     out[0] = sh[0][0] + sh[1][0];
     out[1] = sh[2][0] + sh[3][0];
     out[2] = sh[4][0];
+    // the unrounded compensated sum (re_hi, re_lo, im_hi, im_lo, sum |p|) for range partials
+    for (int j = 0; j < 5; ++j) out[3 + j] = sh[j][0];
   }
 }
 
@@ -438,7 +443,7 @@ bool make_plan(int N, const DeviceInfo& dev, int warps_main, int kcap_override, 
   plan.off_partials = off; off = align256(off + sizeof(double) * 5 * (size_t)plan.nclass * plan.nchunks);
   plan.off_counters = off; off = align256(off + sizeof(unsigned) * kMaxClasses);
   plan.off_blocks = off; off = align256(off + sizeof(double) * 5 * kReduceBlocks);
-  plan.off_out = off; off = align256(off + sizeof(double) * 4);
+  plan.off_out = off; off = align256(off + sizeof(double) * 8);
   plan.bytes = off;
   *p = plan;
   return true;
@@ -497,7 +502,8 @@ static cudaError_t side_streams(cudaStream_t** out) {
 // ordered after what precedes it on `stream` and before what follows.
 template <bool kVisit>
 static cudaError_t launch_classes(const LhafPlan& plan, void* ws, unsigned* visits,
-                                  cudaStream_t stream) {
+                                  cudaStream_t stream, uint64_t i_base, uint64_t i_end,
+                                  unsigned nchunks) {
   char* b = static_cast<char*>(ws);
   unsigned* counters = reinterpret_cast<unsigned*>(b + plan.off_counters);
   double* partials = reinterpret_cast<double*>(b + plan.off_partials);
@@ -521,12 +527,12 @@ static cudaError_t launch_classes(const LhafPlan& plan, void* ws, unsigned* visi
     const size_t smem = (size_t)cp.warps * cp.area_elems * plan.esz;
     if (!kVisit && plan.prec == kPrecTF)
       lhaf_subsets_kernel<tfc, false><<<cp.blocks, 32 * cp.warps, smem, sc>>>(
-          P, cp.k_lo, cp.k_hi, cp.area_elems, plan.chunk_size, plan.nchunks, counters + c,
-          partials + (size_t)c * plan.nchunks * 5, visits);
+          P, cp.k_lo, cp.k_hi, cp.area_elems, plan.chunk_size, i_base, i_end, nchunks,
+          counters + c, partials + (size_t)c * plan.nchunks * 5, visits);
     else
       lhaf_subsets_kernel<double2, kVisit><<<cp.blocks, 32 * cp.warps, smem, sc>>>(
-          P, cp.k_lo, cp.k_hi, cp.area_elems, plan.chunk_size, plan.nchunks, counters + c,
-          partials + (size_t)c * plan.nchunks * 5, visits);
+          P, cp.k_lo, cp.k_hi, cp.area_elems, plan.chunk_size, i_base, i_end, nchunks,
+          counters + c, partials + (size_t)c * plan.nchunks * 5, visits);
     e = cudaGetLastError();
     if (e == cudaSuccess && c > 0) {
       cudaEvent_t join = nullptr;
@@ -540,19 +546,35 @@ static cudaError_t launch_classes(const LhafPlan& plan, void* ws, unsigned* visi
   return e;
 }
 
-cudaError_t launch_lhaf(const LhafPlan& plan, const double2* base, int ld, const double2* diag,
-                        const int* idx, void* ws, cudaStream_t stream) {
+// Subsets of the enumeration indices [i_begin, i_end) (z = i ^ (i >> 1)), in chunks of the
+// plan's chunk size starting at i_begin, then the two-level fixed-order finalize.
+static cudaError_t launch_range(const LhafPlan& plan, const double2* base, int ld,
+                                const double2* diag, const int* idx, void* ws,
+                                cudaStream_t stream, uint64_t i_begin, uint64_t i_end) {
   cudaError_t e = launch_expand(plan, base, ld, diag, idx, ws, stream);
   if (e != cudaSuccess) return e;
-  e = launch_classes<false>(plan, ws, nullptr, stream);
+  const uint64_t span = i_end > i_begin ? i_end - i_begin : 0;
+  const unsigned nchunks = (unsigned)((span + plan.chunk_size - 1) / plan.chunk_size);
+  e = launch_classes<false>(plan, ws, nullptr, stream, i_begin, i_end, nchunks);
   if (e != cudaSuccess) return e;
   char* b = static_cast<char*>(ws);
   double* blocks = reinterpret_cast<double*>(b + plan.off_blocks);
   lhaf_partials_kernel<<<kReduceBlocks, kFinalizeThreads, 0, stream>>>(
-      reinterpret_cast<const double*>(b + plan.off_partials), plan.nchunks, plan.nclass, blocks);
+      reinterpret_cast<const double*>(b + plan.off_partials), nchunks, plan.nchunks, plan.nclass,
+      blocks);
   lhaf_finalize_kernel<<<1, kFinalizeThreads, 0, stream>>>(blocks, kReduceBlocks,
                                                            reinterpret_cast<double*>(b + plan.off_out));
   return cudaGetLastError();
+}
+
+cudaError_t launch_lhaf(const LhafPlan& plan, const double2* base, int ld, const double2* diag,
+                        const int* idx, void* ws, cudaStream_t stream) {
+  return launch_range(plan, base, ld, diag, idx, ws, stream, 0, (uint64_t)1 << plan.n);
+}
+
+cudaError_t launch_lhaf_range(const LhafPlan& plan, const double2* base, int ld, void* ws,
+                              cudaStream_t stream, uint64_t i_begin, uint64_t i_end) {
+  return launch_range(plan, base, ld, nullptr, nullptr, ws, stream, i_begin, i_end);
 }
 
 cudaError_t launch_subset_terms(const LhafPlan& plan, const double2* base, int ld,
@@ -591,7 +613,7 @@ cudaError_t launch_write_unit(double2* out, double* abs_sum, cudaStream_t stream
 
 cudaError_t launch_visit_count(const LhafPlan& plan, unsigned* counts, void* ws,
                                cudaStream_t stream) {
-  return launch_classes<true>(plan, ws, counts, stream);
+  return launch_classes<true>(plan, ws, counts, stream, 0, (uint64_t)1 << plan.n, plan.nchunks);
 }
 
 }  // namespace gbsh

@@ -55,6 +55,12 @@ bool make_plan(int N, const DeviceInfo& dev, int warps_main, int kcap_override, 
 cudaError_t launch_lhaf(const LhafPlan& plan, const double2* base, int ld, const double2* diag,
                         const int* idx, void* ws, cudaStream_t stream);
 
+// The subsets of the enumeration indices [i_begin, i_end) only (z = i ^ (i >> 1); any
+// partition of [0, 2^n) into such ranges covers every subset once). Writes the range's
+// compensated partial (re_hi, re_lo, im_hi, im_lo, sum |p_Z|) to ws + off_out + 3 doubles.
+cudaError_t launch_lhaf_range(const LhafPlan& plan, const double2* base, int ld, void* ws,
+                              cudaStream_t stream, uint64_t i_begin, uint64_t i_end);
+
 // Writes lhaf = 1 (the empty matrix) to out[0] and 0 to *abs_sum (if not null) with a
 // one-thread kernel on `stream`.
 cudaError_t launch_write_unit(double2* out, double* abs_sum, cudaStream_t stream);

@@ -67,6 +67,8 @@ def load() -> ctypes.CDLL:
         "gbsh_lhaf_plan_ex": ([i, i] + [ctypes.POINTER(ctypes.c_int)] * 5, i),
         "gbsh_lhaf_noalloc": ([vp, i, i, vp, vp, vp], i),
         "gbsh_lhaf_noalloc_plan": ([i, ctypes.POINTER(ctypes.c_int)], i),
+        "gbsh_lhaf_range_async": ([vp, i, i, i, ctypes.c_uint64, ctypes.c_uint64, vp, vp, sz, vp], i),
+        "gbsh_combine_partials": ([vp, i, vp], i),
         "gbsh_lhaf_batch": ([vp, vp, vp, i, vp, vp, i, vp], i),
         "gbsh_gbs_prob_batch": ([vp, i, i, vp, ctypes.c_int64, vp, i, vp, vp, vp, i, vp], i),
         "gbsh_set_batch_tuning": ([i, i, i], i),
@@ -88,7 +90,7 @@ def exported_symbols():
             "gbsh_gbs_prob_batch", "gbsh_set_batch_tuning", "gbsh_set_batch_graphs",
             "gbsh_batch_graph_stats", "gbsh_lhaf_ex", "gbsh_lhaf_async_ex",
             "gbsh_lhaf_workspace_size_ex", "gbsh_subset_terms_ex", "gbsh_lhaf_plan_ex",
-            "gbsh_lhaf_noalloc_plan"]
+            "gbsh_lhaf_noalloc_plan", "gbsh_lhaf_range_async", "gbsh_combine_partials"]
 
 
 def _strerror(code: int) -> str:
@@ -201,6 +203,45 @@ def lhaf_noalloc(dA, d_out, d_abs_sum=None, stream=None):
         ctypes.c_void_p(d_abs_sum.data_ptr() if d_abs_sum is not None else 0),
         ctypes.c_void_p(_stream_handle(stream)))
     _check(rc, "gbsh_lhaf_noalloc")
+
+
+def lhaf_range(dA, i_begin: int, i_end: int, precision=PREC_FP64, stream=None):
+    """Compensated partial (re_hi, re_lo, im_hi, im_lo, sum|p|) of the subsets with
+    enumeration indices in [i_begin, i_end) (gbsh_lhaf_range_async), as a numpy array;
+    synchronises the stream."""
+    import torch
+    ptr, N, ld, _ = _as_matrix(dA)
+    ws = torch.empty(workspace_size(N, precision), dtype=torch.uint8, device=dA.device)
+    part = torch.empty(5, dtype=torch.float64, device=dA.device)
+    st = ctypes.c_void_p(_stream_handle(stream))
+    rc = load().gbsh_lhaf_range_async(ctypes.c_void_p(ptr), N, ld, int(precision), int(i_begin),
+                                      int(i_end), ctypes.c_void_p(part.data_ptr()),
+                                      ctypes.c_void_p(ws.data_ptr()), ws.numel(), st)
+    _check(rc, "gbsh_lhaf_range_async")
+    out = part.cpu().numpy()
+    return out
+
+
+def combine_partials(partials) -> np.ndarray:
+    """gbsh_combine_partials: fixed-order compensated sum of range partials (k x 5)."""
+    p = np.ascontiguousarray(partials, dtype=np.float64).reshape(-1, 5)
+    out = np.zeros(5)
+    _check(load().gbsh_combine_partials(ctypes.c_void_p(p.ctypes.data), p.shape[0],
+                                        ctypes.c_void_p(out.ctypes.data)), "gbsh_combine_partials")
+    return out
+
+
+def partial_value(p) -> complex:
+    """The complex value (re_hi + re_lo) + i (im_hi + im_lo) of a (combined) partial."""
+    return complex(p[0] + p[1], p[2] + p[3])
+
+
+def range_bounds(N: int, rank: int, world: int):
+    """[i_begin, i_end) of rank `rank` when the 2^n enumeration indices of an N x N loop
+    hafnian are split into `world` contiguous ranges of (nearly) equal length."""
+    n = (N + (N & 1)) // 2
+    total = 1 << n
+    return total * rank // world, total * (rank + 1) // world
 
 
 def noalloc_chunks(N: int) -> int:
