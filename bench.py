@@ -708,6 +708,44 @@ def fig2_allones(sizes_fp64=range(30, 58, 2), sizes_dd=range(30, 48, 2)):
     return rows
 
 
+def accuracy_table():
+    """Relative error of both paths (FP64, triple-float) on every committed oracle fixture
+    (tests/golden: the configuration matrices N=32/40/50, the repeated-mode N=40 matrix, the
+    block-diagonal N=50/56 matrices) and on all-ones matrices (exact T(n)), with each
+    evaluation's time."""
+    import numpy as np
+    import torch
+    from fractions import Fraction
+    from paper_2010_15595_gb300 import lib
+    rows = []
+    for name, tol in (("lhaf_n32", 1e-9), ("lhaf_n40", 1e-9), ("lhaf_n40_repeated", 1e-9),
+                      ("lhaf_n50", 1e-7), ("lhaf_n50_block", 1e-7), ("lhaf_n56_block", 1e-7)):
+        g = golden_reference(name)
+        if g is None:
+            continue
+        dA = torch.from_numpy(g[0]).cuda()
+        row = {"fixture": name, "N": g[0].shape[0], "reference": g[2], "tol_stated": tol}
+        for pname, prec in (("fp64", lib.PREC_FP64), ("tf", lib.PREC_TF)):
+            t = time.perf_counter()
+            v = lib.lhaf(dA, precision=prec)
+            row[pname + "_seconds"] = time.perf_counter() - t
+            row[pname + "_rel_err"] = rel_err(v, g[1])
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+    for n in (40, 56):
+        A = np.ones((n, n), dtype=np.complex128)
+        T = telephone(n)
+        row = {"fixture": f"all-ones {n}", "N": n, "reference": "T(n), exact", "tol_stated": 1e-9 if n <= 40 else 1e-7}
+        for pname, prec in (("fp64", lib.PREC_FP64), ("tf", lib.PREC_TF)):
+            t = time.perf_counter()
+            v = lib.lhaf(A, precision=prec)
+            row[pname + "_seconds"] = time.perf_counter() - t
+            row[pname + "_rel_err"] = float(abs(Fraction(v.real) - T) / T)
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+    return rows
+
+
 # ------------------------------------------------------------------ reference arm
 
 def run_reference(args, rank, world):
@@ -766,12 +804,18 @@ def main(argv=None):
     p.add_argument("--fig2", action="store_true",
                    help="run the Fig. 2 all-ones accuracy study (Sec. IV) instead of the benchmark")
     p.add_argument("--fig1-unitaries", type=int, default=10)
+    p.add_argument("--accuracy", action="store_true",
+                   help="errors of both paths on the committed oracle fixtures, then exit")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--ref-step-seconds", type=float, default=4.0)
     args = p.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
+    if args.accuracy:
+        rows = accuracy_table()
+        print(json.dumps({"experiment": "accuracy of both paths on the oracle fixtures", "rows": rows}), flush=True)
+        return
     if args.fig2:
         rows = fig2_allones()
         print(json.dumps({"experiment": "Fig. 2 all-ones accuracy", "rows": rows}), flush=True)
