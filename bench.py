@@ -135,7 +135,18 @@ class ClockSampler:
 # Sources that define the subset kernel, its launches and its finalize (the sampler and the
 # C-ABI wrappers do not change what one evaluation moves through DRAM).
 KERNEL_SOURCES = ("lhaf_core.cuh", "lhaf_kernels.cu", "lhaf_kernels.cuh", "lhaf_types.cuh",
-                  "lhaf_tf.cuh")
+                  "lhaf_tf.cuh", "tuned_gb300.inc")
+
+
+def tuning_block(N: int) -> dict:
+    """Launch-shape table entries in force for size N (autotune.py; 0 = library default)."""
+    from paper_2010_15595_gb300 import lib
+    nb = lib.builtin_tuning_entries()
+    return {"source": (f"built-in table measured by autotune.py on a GB300 ({nb} entries)"
+                       if nb else "library defaults (no measured entries)"),
+            "tf": dict(zip(("warps_cap", "ladder", "log2_chunks"), lib.get_lhaf_tuning(lib.PREC_TF, N))),
+            "fp64": dict(zip(("warps_cap", "ladder", "log2_chunks"), lib.get_lhaf_tuning(lib.PREC_FP64, N))),
+            "batch_fp64_n15": dict(zip(("warps_small", "warps_large"), lib.get_batch_tuning(lib.PREC_FP64, 15)))}
 
 
 def kernel_source_hash() -> str:
@@ -447,7 +458,8 @@ def run_ours(args, rank, world, local_rank):
                        "path": "triple-float per subset (GBSH_PREC_TF: three FP32 words, "
                                "~72-bit significand), compensated FP64 cross-subset sum",
                        "l2": "flushed between timed steps (256 MiB write, outside the events)",
-                       "plan": plan, "parallelism": f"replicas x{world}"},
+                       "plan": plan, "tuning": tuning_block(N),
+                       "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "alu", "achieved": tf_ach, "peak": tf_peak,
                          "unit": "T FP32 instr/s", "frac": tf_ach / tf_peak,
                          "traffic": recorded_traffic(N, "tf"),

@@ -183,9 +183,43 @@ int gbsh_gbs_prob_batch(const gbsh_c128* B, int M, int ldb, const gbsh_c128* gam
                         const double* p_vacs, double* probs, gbsh_c128* lhafs, int precision,
                         void* stream);
 
-/* Warps per CTA used by the batched kernel for batches whose largest matrix has n_max
- * pairs (N = 2 n_max), per precision (0 = built-in default). Set by the autotuner. */
+/* Warps per CTA of the large-popcount class of the batched kernel for batches whose largest
+ * matrix has n_max pairs (N = 2 n_max), per precision (0 = the tuning table's value); the
+ * small-popcount class keeps its setting. Results do not depend on it. GBSH_OK or
+ * GBSH_EINVAL (precision GBSH_PREC_MIXED, n_max outside 0..30, warps outside 0..16). */
 int gbsh_set_batch_tuning(int precision, int n_max, int warps_per_cta);
+
+/*
+ * Launch-shape tuning table. The library's default launch shapes come from a built-in table
+ * that the autotuner (autotune.py) measured on a GB300; these calls override or read its
+ * entries for this process. A launch shape never changes which subsets are summed:
+ *
+ * gbsh_set_batch_tuning_ex — batched kernel, batches whose largest matrix has n_max pairs:
+ *   warps per CTA of the small-popcount class (popcounts <= 10) and of the large-popcount
+ *   class (1..16; 0 in both restores the built-in entry, 0 in one selects the library
+ *   default for that class). Results are bit-identical under any setting.
+ * gbsh_set_lhaf_tuning_ex — single evaluations (gbsh_lhaf*, gbsh_gbs_prob, the range and
+ *   no-allocation entries) of size N in precision GBSH_PREC_FP64 or GBSH_PREC_TF:
+ *   warps_cap  most warps per CTA of any popcount class (1..16; 0 = 12 FP64, 16 TF)
+ *   ladder     1 coarse {16,12,8,6,4,3,2,1} or 2 fine {16,14,12,10,8,7,6,5,4,3,2,1}: the
+ *              warps-per-CTA steps by which popcounts are assigned to classes (0 = coarse)
+ *   log2_chunks  enumeration chunks of one evaluation, 2^log2_chunks capped at 2^(N/2)
+ *              (1..18; 0 = 18)
+ *   All three 0 restores the built-in entry. The ladder and chunk count regroup the
+ *   compensated cross-subset sum, so results agree with other settings to its rounding and
+ *   are bit-reproducible under any one setting. gbsh_set_lhaf_tuning's process-wide
+ *   override, while set, takes precedence over this table. Ranks that split one evaluation
+ *   with gbsh_lhaf_range_async must use the same entry.
+ * gbsh_get_lhaf_tuning / gbsh_get_batch_tuning — the current entry (0 = library default).
+ * gbsh_builtin_tuning_entries — number of measured entries in the built-in table.
+ * All return GBSH_OK or GBSH_EINVAL (arguments outside the ranges above); output pointers may
+ * be NULL.
+ */
+int gbsh_set_batch_tuning_ex(int precision, int n_max, int warps_small, int warps_large);
+int gbsh_set_lhaf_tuning_ex(int precision, int N, int warps_cap, int ladder, int log2_chunks);
+int gbsh_get_lhaf_tuning(int precision, int N, int* warps_cap, int* ladder, int* log2_chunks);
+int gbsh_get_batch_tuning(int precision, int n_max, int* warps_small, int* warps_large);
+int gbsh_builtin_tuning_entries(void);
 
 /* CUDA-graph replay of the batched evaluations (gbsh_lhaf_batch, gbsh_gbs_prob_batch and the
  * sampler's ticks). The device work of one batched evaluation -- expansion, the persistent
@@ -268,21 +302,25 @@ int gbsh_subset_terms_ex(const gbsh_c128* dA, int N, int lda, int precision, con
 int gbsh_visit_counts(int N, unsigned* d_counts, void* stream);
 
 /*
- * gbsh_set_lhaf_tuning — launch shape of the subset kernel for subsequent calls on this
- * process: warps per CTA (1..16, 0 = default 8) and a cap on the popcount handled by the
- * many-warp class (0 = largest that fits in shared memory). Subsets above the cap run in
- * a second launch with fewer warps and larger work areas. Results do not depend on it.
+ * gbsh_set_lhaf_tuning — process-wide launch-shape override of the subset kernel for
+ * subsequent single evaluations of every size and precision: a cap on warps per CTA (1..16)
+ * and a cap on the popcount handled by the first (many-warp) class (0 = largest that fits in
+ * shared memory); subsets above it run in further launches with fewer warps and larger work
+ * areas. While either value is nonzero it replaces the tuning table (gbsh_set_lhaf_tuning_ex)
+ * with the coarse ladder and 2^18 chunks; (0, 0) returns to the table. The warps cap does not
+ * change results; the popcount cap regroups the cross-subset sum (agreement to its rounding).
  */
 int gbsh_set_lhaf_tuning(int warps_per_cta, int kcap);
 
 /*
  * gbsh_lhaf_plan — launch plan that gbsh_lhaf / gbsh_lhaf_async use for size N on the
  * current device, under the current tuning. Any output pointer may be NULL.
- *   nclass     number of subset-kernel launches (popcount classes, 1..3)
+ *   nclass     number of subset-kernel launches (popcount classes, 1..12)
  *   kernels    CUDA kernels launched per evaluation (expansion + classes + two-level finalize)
  *   warps      warps per CTA of the first class
  *   kcap       largest popcount of the first class
- *   nchunks    number of fixed subset chunks (the reduction order depends only on this)
+ *   nchunks    number of fixed subset chunks (with the popcount classes, it fixes the
+ *              reduction order)
  * Errors: GBSH_EINVAL for N outside 1..GBSH_MAX_N, GBSH_ECUDA without a device.
  */
 int gbsh_lhaf_plan(int N, int* nclass, int* kernels, int* warps, int* kcap, int* nchunks);

@@ -7,6 +7,7 @@
 
 #include "batch_host.h"
 #include "lhaf_kernels.cuh"
+#include "tuning.h"
 
 namespace gbsh {
 
@@ -24,12 +25,12 @@ size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 // cudaGraphLaunch from then on; graph and direct launches run the same kernels with the same
 // arguments, so results are bit-identical.
 struct GraphKey {
-  int dev, count, n_max, precision, warps;
+  int dev, count, n_max, precision, warps, warps_small;
   unsigned total_chunks;
   const char *in, *prob, *counter, *partials, *out;
   bool operator==(const GraphKey& o) const {
     return dev == o.dev && count == o.count && n_max == o.n_max && precision == o.precision &&
-           warps == o.warps && total_chunks == o.total_chunks && in == o.in && prob == o.prob &&
+           warps == o.warps && warps_small == o.warps_small && total_chunks == o.total_chunks && in == o.in && prob == o.prob &&
            counter == o.counter && partials == o.partials && out == o.out;
   }
 };
@@ -90,7 +91,7 @@ cudaError_t graph_store_and_launch(const GraphKey& key, cudaGraphExec_t exec, cu
 // Captures launch_batch for `key` into an executable graph (nullptr on any failure: the
 // caller then launches directly).
 cudaGraphExec_t graph_capture(const GraphKey& key, const BatchLayout& L, char* w, int count,
-                              int precision, int W) {
+                              int precision, int W, int W0) {
   if (key.dev < 0 || key.dev >= 64) return nullptr;
   {
     std::lock_guard<std::mutex> lk(g_graph_mu);
@@ -113,7 +114,7 @@ cudaGraphExec_t graph_capture(const GraphKey& key, const BatchLayout& L, char* w
   }
   cudaError_t e = launch_batch(reinterpret_cast<const BatchInput*>(w + L.off_in),
                                reinterpret_cast<const BatchProblem*>(w + L.off_prob), count,
-                               L.total_chunks, L.n_max, precision, W,
+                               L.total_chunks, L.n_max, precision, W, W0,
                                reinterpret_cast<unsigned*>(w + L.off_counter),
                                reinterpret_cast<double*>(w + L.off_partials),
                                reinterpret_cast<double*>(w + L.off_out), cs, g_cap_side[key.dev]);
@@ -202,19 +203,22 @@ cudaError_t batch_run(BatchLayout& L, const std::vector<BatchInput>& in, int cou
   if (e != cudaSuccess) return e;
   e = ensure_constants();
   if (e != cudaSuccess) return e;
-  const int W = batch_warps_for(std::max(L.n_max, 1), precision, dev, warps_pref);
+  const BatchTuning bt = batch_tuning(precision, L.n_max);
+  const int W = batch_warps_for(std::max(L.n_max, 1), precision, dev,
+                                warps_pref > 0 ? warps_pref : bt.warps_large);
   if (W < 1) return cudaErrorInvalidValue;
+  const int W0 = bt.warps_small;
   bool launched = false;
   if (g_graphs_enabled.load() && count > 0) {
     int d = 0;
     e = cudaGetDevice(&d);
     if (e != cudaSuccess) return e;
-    const GraphKey key{d, count, L.n_max, precision, W, L.total_chunks, w + L.off_in,
+    const GraphKey key{d, count, L.n_max, precision, W, W0, L.total_chunks, w + L.off_in,
                        w + L.off_prob, w + L.off_counter, w + L.off_partials, w + L.off_out};
     bool capture_now = false;
     launched = graph_try_launch(key, st, &capture_now, &e);
     if (!launched && capture_now) {
-      cudaGraphExec_t exec = graph_capture(key, L, w, count, precision, W);
+      cudaGraphExec_t exec = graph_capture(key, L, w, count, precision, W, W0);
       if (exec) {
         e = graph_store_and_launch(key, exec, st);
         launched = true;
@@ -225,7 +229,7 @@ cudaError_t batch_run(BatchLayout& L, const std::vector<BatchInput>& in, int cou
   if (!launched) {
     e = launch_batch(reinterpret_cast<const BatchInput*>(w + L.off_in),
                      reinterpret_cast<const BatchProblem*>(w + L.off_prob), count, L.total_chunks,
-                     L.n_max, precision, W, reinterpret_cast<unsigned*>(w + L.off_counter),
+                     L.n_max, precision, W, W0, reinterpret_cast<unsigned*>(w + L.off_counter),
                      reinterpret_cast<double*>(w + L.off_partials),
                      reinterpret_cast<double*>(w + L.off_out), st);
   }

@@ -26,7 +26,8 @@ BatchLayout batch_layout(const int* Ns, int count, size_t base_off);
 // Fills the device tables of `L` (inputs `in` indexed by problem, device pointers into
 // memory that is ready on `st`), launches expansion + persistent evaluation + finalize,
 // and copies (re, im, sum|p_Z|) per problem into host `out3` in problem order,
-// synchronising `st`. warps_pref = 0 selects the default launch shape.
+// synchronising `st`. warps_pref > 0 sets the warps per CTA of the large-popcount class;
+// 0 takes the tuning table's launch shape (tuning.h).
 // Returns cudaErrorInvalidValue if no launch shape fits.
 cudaError_t batch_run(BatchLayout& L, const std::vector<BatchInput>& in, int count, int precision,
                       int warps_pref, void* ws, cudaStream_t st, double* out3);

@@ -14,6 +14,7 @@
 #include "../../include/gbsh.h"
 #include "batch_host.h"
 #include "lhaf_kernels.cuh"
+#include "tuning.h"
 
 namespace {
 
@@ -89,8 +90,11 @@ int plan_for(int N, gbsh::LhafPlan* plan, int prec = GBSH_PREC_FP64) {
     k = g_tune_kcap;
   }
   const int kprec = prec == GBSH_PREC_TF ? gbsh::kPrecTF : gbsh::kPrecFP64;
-  if (!gbsh::make_plan(N, dev, w, k, plan, gbsh::kTargetChunks, kprec)) return GBSH_EINVAL;
-  return GBSH_OK;
+  // a process-wide override (gbsh_set_lhaf_tuning) replaces the per-size tuning table
+  const bool ok = (w != 0 || k != 0)
+                      ? gbsh::make_plan(N, dev, w, k, plan, gbsh::kTargetChunks, kprec)
+                      : gbsh::make_tuned_plan(N, dev, kprec, plan);
+  return ok ? GBSH_OK : GBSH_EINVAL;
 }
 
 // Unit roundoff of a precision's per-subset arithmetic (for the error estimate).
@@ -128,18 +132,12 @@ double err_from(double abs_sum, gbsh_c128 v, int prec = GBSH_PREC_FP64) {
 
 
 // ---------------------------------------------------------------- batched evaluation
-int g_batch_warps[gbsh::kNumPrec][gbsh::kMaxN / 2 + 1] = {};  // per precision and n_max; 0 = default
 using gbsh::BatchLayout;
 using gbsh::batch_layout;
 
 int batch_run(BatchLayout& L, const std::vector<gbsh::BatchInput>& in, int count, int precision,
               void* ws, cudaStream_t st, double* out3) {
-  int pref;
-  {
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    pref = g_batch_warps[precision][L.n_max];
-  }
-  cudaError_t e = gbsh::batch_run(L, in, count, precision, pref, ws, st, out3);
+  cudaError_t e = gbsh::batch_run(L, in, count, precision, 0, ws, st, out3);
   if (e == cudaErrorInvalidValue) return GBSH_EINVAL;
   if (e != cudaSuccess) return cuda_fail(e);
   return GBSH_OK;
@@ -584,10 +582,54 @@ int gbsh_set_batch_tuning(int precision, int n_max, int warps_per_cta) {
     return GBSH_EINVAL;
   if (n_max < 0 || n_max > gbsh::kMaxN / 2 || warps_per_cta < 0 || warps_per_cta > gbsh::kMaxWarps)
     return GBSH_EINVAL;
-  std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_batch_warps[precision][n_max] = warps_per_cta;
+  gbsh::BatchTuning t = gbsh::batch_tuning(precision, n_max);
+  t.warps_large = warps_per_cta;
+  gbsh::set_batch_tuning(precision, n_max, t);
   return GBSH_OK;
 }
+
+int gbsh_set_batch_tuning_ex(int precision, int n_max, int warps_small, int warps_large) {
+  if (precision != GBSH_PREC_FP64 && precision != GBSH_PREC_C32 && precision != GBSH_PREC_DD &&
+      precision != GBSH_PREC_TF)
+    return GBSH_EINVAL;
+  if (n_max < 0 || n_max > gbsh::kMaxN / 2 || warps_small < 0 || warps_small > gbsh::kMaxWarps ||
+      warps_large < 0 || warps_large > gbsh::kMaxWarps)
+    return GBSH_EINVAL;
+  gbsh::set_batch_tuning(precision, n_max, gbsh::BatchTuning{warps_small, warps_large});
+  return GBSH_OK;
+}
+
+int gbsh_set_lhaf_tuning_ex(int precision, int N, int warps_cap, int ladder, int log2_chunks) {
+  if (!valid_single_precision(precision) || N < 1 || N > GBSH_MAX_N) return GBSH_EINVAL;
+  if (warps_cap < 0 || warps_cap > gbsh::kMaxWarps || ladder < 0 || ladder > 2 ||
+      log2_chunks < 0 || log2_chunks > 18)
+    return GBSH_EINVAL;
+  const int kprec = precision == GBSH_PREC_TF ? gbsh::kPrecTF : gbsh::kPrecFP64;
+  gbsh::set_single_tuning(kprec, N, gbsh::SingleTuning{warps_cap, ladder, log2_chunks});
+  return GBSH_OK;
+}
+
+int gbsh_get_lhaf_tuning(int precision, int N, int* warps_cap, int* ladder, int* log2_chunks) {
+  if (!valid_single_precision(precision) || N < 1 || N > GBSH_MAX_N) return GBSH_EINVAL;
+  const int kprec = precision == GBSH_PREC_TF ? gbsh::kPrecTF : gbsh::kPrecFP64;
+  const gbsh::SingleTuning t = gbsh::single_tuning(kprec, N);
+  if (warps_cap) *warps_cap = t.warps_cap;
+  if (ladder) *ladder = t.ladder;
+  if (log2_chunks) *log2_chunks = t.log2_chunks;
+  return GBSH_OK;
+}
+
+int gbsh_get_batch_tuning(int precision, int n_max, int* warps_small, int* warps_large) {
+  if (precision < 0 || precision >= gbsh::kNumPrec || precision == GBSH_PREC_MIXED || n_max < 0 ||
+      n_max > gbsh::kMaxN / 2)
+    return GBSH_EINVAL;
+  const gbsh::BatchTuning t = gbsh::batch_tuning(precision, n_max);
+  if (warps_small) *warps_small = t.warps_small;
+  if (warps_large) *warps_large = t.warps_large;
+  return GBSH_OK;
+}
+
+int gbsh_builtin_tuning_entries(void) { return gbsh::builtin_tuning_entries(nullptr, nullptr); }
 
 int gbsh_set_batch_graphs(int enable) {
   gbsh::set_batch_graphs(enable != 0);

@@ -9,13 +9,15 @@
 //                           from a counter; one compensated partial per chunk.
 //   lhaf_finalize_kernel    fixed-order compensated reduction of the chunk partials.
 //
-// The result depends only on the chunking (a function of N), not on the launch shape or
-// on which warp took which chunk, so it is bit-reproducible.
+// The result depends only on the chunking (the chunk count of the plan) and the popcount
+// classes, not on the warps per CTA or on which warp took which chunk, so a given plan is
+// bit-reproducible.
 #include <cmath>
 #include <mutex>
 
 #include "lhaf_core.cuh"
 #include "lhaf_kernels.cuh"
+#include "tuning.h"
 
 namespace gbsh {
 
@@ -377,7 +379,7 @@ cudaError_t ensure_constants() {
 }
 
 bool make_plan(int N, const DeviceInfo& dev, int warps_main, int kcap_override, LhafPlan* p,
-               unsigned max_chunks, int prec) {
+               unsigned max_chunks, int prec, int ladder) {
   if (N < 1 || N > kMaxN) return false;
   if (prec != kPrecFP64 && prec != kPrecTF) return false;
   LhafPlan plan{};
@@ -405,11 +407,17 @@ bool make_plan(int N, const DeviceInfo& dev, int warps_main, int kcap_override, 
   // per CTA, W_c the largest count of a fixed ladder (capped at W) whose work areas fit.
   // Most subsets (popcount near n/2) have small matrices and run with many warps per SM to
   // hide the FP64 latency; the few large ones run with larger work areas.
-  static const int kLadder[] = {16, 12, 8, 6, 4, 3, 2, 1};
+  // The fine ladder adds intermediate steps, so that more popcounts run with more warps (at
+  // the cost of more class launches and partial sums).
+  static const int kCoarse[] = {16, 12, 8, 6, 4, 3, 2, 1};
+  static const int kFine[] = {16, 14, 12, 10, 8, 7, 6, 5, 4, 3, 2, 1};
+  const int* lad = ladder == kLadderFine ? kFine : kCoarse;
+  const int nlad = ladder == kLadderFine ? (int)(sizeof(kFine) / sizeof(kFine[0]))
+                                         : (int)(sizeof(kCoarse) / sizeof(kCoarse[0]));
   plan.nclass = 0;
   int k_done = 0;
-  for (int wi = 0; wi < (int)(sizeof(kLadder) / sizeof(kLadder[0])) && k_done < n; ++wi) {
-    const int Wc = kLadder[wi];
+  for (int wi = 0; wi < nlad && k_done < n; ++wi) {
+    const int Wc = lad[wi];
     if (Wc > W) continue;
     int kc = kfit(Wc);
     if (plan.nclass == 0 && kcap_override > 0 && kcap_override < kc) kc = kcap_override;
@@ -447,6 +455,14 @@ bool make_plan(int N, const DeviceInfo& dev, int warps_main, int kcap_override, 
   plan.bytes = off;
   *p = plan;
   return true;
+}
+
+bool make_tuned_plan(int N, const DeviceInfo& dev, int prec, LhafPlan* p, unsigned max_chunks) {
+  const SingleTuning t = single_tuning(prec, N);
+  unsigned cap = max_chunks;
+  if (t.log2_chunks >= 1 && t.log2_chunks <= 18 && (1u << t.log2_chunks) < cap)
+    cap = 1u << t.log2_chunks;
+  return make_plan(N, dev, t.warps_cap, 0, p, cap, prec, t.ladder);
 }
 
 static Problem problem_of(const LhafPlan& plan, void* ws) {
@@ -674,7 +690,7 @@ int batch_classes(int n_max) { return n_max > kBatchSplitK ? 2 : 1; }
 
 cudaError_t launch_batch(const BatchInput* d_in, const BatchProblem* d_prob, int count,
                          unsigned total_chunks, int n_max, int precision, int warps,
-                         unsigned* d_counter, double* d_partials, double* d_out,
+                         int warps_small, unsigned* d_counter, double* d_partials, double* d_out,
                          cudaStream_t stream, cudaStream_t side_stream) {
   if (count <= 0) return cudaSuccess;
   DeviceInfo dev;
@@ -695,7 +711,7 @@ cudaError_t launch_batch(const BatchInput* d_in, const BatchProblem* d_prob, int
     } else {
       // Class 0 (popcount <= kBatchSplitK, most subsets): small work areas, many warps.
       const int area0 = warp_area_elems(kBatchSplitK, nm, esz);
-      int W0 = kMaxWarps;
+      int W0 = warps_small > 0 && warps_small < kMaxWarps ? warps_small : kMaxWarps;
       while (W0 > 1 && (size_t)W0 * area0 * esz > (size_t)dev.smem_optin) --W0;
       // Class 1 (larger popcounts) on a side stream, forked from and joined into `stream`.
       cudaStream_t sc = side_stream;

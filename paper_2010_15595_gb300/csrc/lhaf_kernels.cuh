@@ -12,7 +12,7 @@ namespace gbsh {
 constexpr int kMaxWarps = 16;          // warps per CTA of the subset kernel
 constexpr int kFinalizeThreads = 256;  // threads of the finalize kernels
 constexpr int kReduceBlocks = 128;     // CTAs of the first level of the final reduction
-constexpr int kMaxClasses = 8;         // popcount classes of one evaluation
+constexpr int kMaxClasses = 12;        // popcount classes of one evaluation
 constexpr unsigned kTargetChunks = 1u << 18;  // Gray-code chunks of one evaluation (at most)
 
 // One launch of the subset kernel: subsets with popcount in [k_lo, k_hi], `warps` warps per
@@ -45,10 +45,14 @@ cudaError_t device_info(DeviceInfo* info);
 cudaError_t ensure_constants();
 // Builds the launch plan. warps_main = 0 selects the default cap on warps per CTA;
 // max_chunks bounds the number of subset chunks (a power of two); prec selects the
-// per-subset arithmetic (kPrecFP64 or kPrecTF). Returns false if N or prec is out of range
-// for the available shared memory.
+// per-subset arithmetic (kPrecFP64 or kPrecTF); ladder is a gbsh::Ladder (tuning.h).
+// Returns false if N or prec is out of range for the available shared memory.
 bool make_plan(int N, const DeviceInfo& dev, int warps_main, int kcap_override, LhafPlan* plan,
-               unsigned max_chunks = kTargetChunks, int prec = kPrecFP64);
+               unsigned max_chunks = kTargetChunks, int prec = kPrecFP64, int ladder = 0);
+// make_plan with the launch shape of the tuning table for (prec, N) (tuning.h); max_chunks
+// further bounds the chunk count.
+bool make_tuned_plan(int N, const DeviceInfo& dev, int prec, LhafPlan* plan,
+                     unsigned max_chunks = kTargetChunks);
 
 // Launches expansion + subset classes + finalize for one problem. `base`, `diag`, `idx` as
 // in expand_problem_kernel. Writes lhaf (re, im) and sum |p_Z| into ws + off_out.
@@ -92,7 +96,7 @@ int batch_classes(int n_max);
 // launch (nullptr: the library's side stream).
 cudaError_t launch_batch(const BatchInput* d_in, const BatchProblem* d_prob, int count,
                          unsigned total_chunks, int n_max, int precision, int warps,
-                         unsigned* d_counter, double* d_partials, double* d_out,
+                         int warps_small, unsigned* d_counter, double* d_partials, double* d_out,
                          cudaStream_t stream, cudaStream_t side_stream = nullptr);
 
 }  // namespace gbsh

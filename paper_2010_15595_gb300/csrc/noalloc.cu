@@ -33,8 +33,9 @@ int fail(cudaError_t e) {
   return e == cudaErrorMemoryAllocation ? GBSH_ENOMEM : GBSH_ECUDA;
 }
 
-// The library default plan for size N, with the chunk count halved until the scratch fits
-// the fixed array: GBSH_OK, or GBSH_ENOMEM when even one chunk does not fit.
+// The library's plan for size N (the tuning table's launch shape), with the chunk count
+// halved until the scratch fits the fixed array: GBSH_OK, or GBSH_ENOMEM when even one chunk
+// does not fit.
 int fit_plan(int N, gbsh::LhafPlan* plan) {
   gbsh::DeviceInfo info;
   cudaError_t e = gbsh::device_info(&info);
@@ -43,7 +44,7 @@ int fit_plan(int N, gbsh::LhafPlan* plan) {
   if (e != cudaSuccess) return fail(e);
   unsigned max_chunks = gbsh::kTargetChunks;
   for (;;) {
-    if (!gbsh::make_plan(N, info, 0, 0, plan, max_chunks)) return GBSH_EINVAL;
+    if (!gbsh::make_tuned_plan(N, info, gbsh::kPrecFP64, plan, max_chunks)) return GBSH_EINVAL;
     if (plan->bytes <= (size_t)GBSH_NOALLOC_SCRATCH_BYTES) return GBSH_OK;
     if (plan->nchunks <= 1u) return GBSH_ENOMEM;
     max_chunks = plan->nchunks / 2;

@@ -319,7 +319,7 @@ int gbsh_sampler::tick(std::vector<Chain>& active) {
         continue;
       }
       gbsh::LhafPlan plan;
-      if (!gbsh::make_plan(Ns[q], dev, 0, 0, &plan)) return GBSH_EINVAL;
+      if (!gbsh::make_tuned_plan(Ns[q], dev, gbsh::kPrecFP64, &plan)) return GBSH_EINVAL;
       rc = ensure_ws(plan.bytes);
       if (rc != GBSH_OK) return rc;
       const gbsh::BatchInput& b = in[q];

@@ -72,6 +72,11 @@ def load() -> ctypes.CDLL:
         "gbsh_lhaf_batch": ([vp, vp, vp, i, vp, vp, i, vp], i),
         "gbsh_gbs_prob_batch": ([vp, i, i, vp, ctypes.c_int64, vp, i, vp, vp, vp, i, vp], i),
         "gbsh_set_batch_tuning": ([i, i, i], i),
+        "gbsh_set_batch_tuning_ex": ([i, i, i, i], i),
+        "gbsh_set_lhaf_tuning_ex": ([i, i, i, i, i], i),
+        "gbsh_get_lhaf_tuning": ([i, i] + [ctypes.POINTER(ctypes.c_int)] * 3, i),
+        "gbsh_get_batch_tuning": ([i, i] + [ctypes.POINTER(ctypes.c_int)] * 2, i),
+        "gbsh_builtin_tuning_entries": ([], i),
         "gbsh_set_batch_graphs": ([i], i),
         "gbsh_batch_graph_stats": ([ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)], i),
     }
@@ -90,7 +95,9 @@ def exported_symbols():
             "gbsh_gbs_prob_batch", "gbsh_set_batch_tuning", "gbsh_set_batch_graphs",
             "gbsh_batch_graph_stats", "gbsh_lhaf_ex", "gbsh_lhaf_async_ex",
             "gbsh_lhaf_workspace_size_ex", "gbsh_subset_terms_ex", "gbsh_lhaf_plan_ex",
-            "gbsh_lhaf_noalloc_plan", "gbsh_lhaf_range_async", "gbsh_combine_partials"]
+            "gbsh_lhaf_noalloc_plan", "gbsh_lhaf_range_async", "gbsh_combine_partials",
+            "gbsh_set_batch_tuning_ex", "gbsh_set_lhaf_tuning_ex", "gbsh_get_lhaf_tuning",
+            "gbsh_get_batch_tuning", "gbsh_builtin_tuning_entries"]
 
 
 def _strerror(code: int) -> str:
@@ -137,7 +144,38 @@ def version() -> int:
 
 
 def set_tuning(warps_per_cta: int = 0, kcap: int = 0):
+    """Process-wide launch-shape override of single evaluations ((0, 0) = tuning table)."""
     _check(load().gbsh_set_lhaf_tuning(warps_per_cta, kcap), "gbsh_set_lhaf_tuning")
+
+
+LADDER_COARSE, LADDER_FINE = 1, 2
+
+
+def set_lhaf_tuning(precision: int, N: int, warps_cap: int = 0, ladder: int = 0,
+                    log2_chunks: int = 0):
+    """Tuning-table entry of single evaluations of size N (all zero = built-in entry)."""
+    _check(load().gbsh_set_lhaf_tuning_ex(precision, N, warps_cap, ladder, log2_chunks),
+           "gbsh_set_lhaf_tuning_ex")
+
+
+def get_lhaf_tuning(precision: int, N: int):
+    """(warps_cap, ladder, log2_chunks) of the current entry; 0 = library default."""
+    v = [ctypes.c_int(0) for _ in range(3)]
+    _check(load().gbsh_get_lhaf_tuning(precision, N, *[ctypes.byref(x) for x in v]),
+           "gbsh_get_lhaf_tuning")
+    return tuple(x.value for x in v)
+
+
+def get_batch_tuning(precision: int, n_max: int):
+    """(warps_small, warps_large) of the current batched entry; 0 = library default."""
+    v = [ctypes.c_int(0) for _ in range(2)]
+    _check(load().gbsh_get_batch_tuning(precision, n_max, *[ctypes.byref(x) for x in v]),
+           "gbsh_get_batch_tuning")
+    return tuple(x.value for x in v)
+
+
+def builtin_tuning_entries() -> int:
+    return load().gbsh_builtin_tuning_entries()
 
 
 def lhaf(A, stream=None, return_error=False, precision=None):
@@ -367,8 +405,16 @@ def gbs_prob_batch(B, gammas, patterns, p_vacs=None, precision=PREC_FP64, stream
     return probs, lh
 
 
-def set_batch_tuning(precision: int, n_max: int, warps_per_cta: int):
-    _check(load().gbsh_set_batch_tuning(precision, n_max, warps_per_cta), "gbsh_set_batch_tuning")
+def set_batch_tuning(precision: int, n_max: int, warps_per_cta: int,
+                     warps_small: int | None = None):
+    """Warps per CTA of the batched kernel's large-popcount class (and, if given, of its
+    small-popcount class) for batches with largest size n_max pairs."""
+    if warps_small is None:
+        _check(load().gbsh_set_batch_tuning(precision, n_max, warps_per_cta),
+               "gbsh_set_batch_tuning")
+    else:
+        _check(load().gbsh_set_batch_tuning_ex(precision, n_max, warps_small, warps_per_cta),
+               "gbsh_set_batch_tuning_ex")
 
 
 def set_batch_graphs(enable: bool):

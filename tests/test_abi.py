@@ -43,3 +43,44 @@ def test_invalid_arguments_rejected_without_gpu():
     assert (out.re, out.im) == (1.0, 0.0)
     assert so.gbsh_set_lhaf_tuning(99, 0) == lib.GBSH_EINVAL
     assert so.gbsh_lhaf_workspace_size(0) == 0
+
+
+def test_tuning_table_set_get_reset_without_gpu():
+    """The launch-shape table is host state: entries can be set, read back and reset to the
+    built-in (measured) entry without a GPU, and out-of-range values are refused."""
+    from paper_2010_15595_gb300 import autotune
+    for prec in (lib.PREC_FP64, lib.PREC_TF):
+        builtin = lib.get_lhaf_tuning(prec, 40)
+        lib.set_lhaf_tuning(prec, 40, 10, lib.LADDER_FINE, 16)
+        assert lib.get_lhaf_tuning(prec, 40) == (10, lib.LADDER_FINE, 16)
+        lib.set_lhaf_tuning(prec, 40)  # all zero: back to the built-in entry
+        assert lib.get_lhaf_tuning(prec, 40) == builtin
+        assert autotune.library_default(prec)[1] == lib.LADDER_COARSE
+    b = lib.get_batch_tuning(lib.PREC_FP64, 15)
+    lib.set_batch_tuning(lib.PREC_FP64, 15, 6, warps_small=12)
+    assert lib.get_batch_tuning(lib.PREC_FP64, 15) == (12, 6)
+    lib.set_batch_tuning(lib.PREC_FP64, 15, 0, warps_small=0)
+    assert lib.get_batch_tuning(lib.PREC_FP64, 15) == b
+    so = lib.load()
+    assert so.gbsh_set_lhaf_tuning_ex(lib.PREC_FP64, 40, 17, 0, 0) == lib.GBSH_EINVAL
+    assert so.gbsh_set_lhaf_tuning_ex(lib.PREC_FP64, 40, 0, 3, 0) == lib.GBSH_EINVAL
+    assert so.gbsh_set_lhaf_tuning_ex(lib.PREC_FP64, 40, 0, 0, 19) == lib.GBSH_EINVAL
+    assert so.gbsh_set_lhaf_tuning_ex(lib.PREC_C32, 40, 8, 0, 0) == lib.GBSH_EINVAL
+    assert so.gbsh_set_lhaf_tuning_ex(lib.PREC_FP64, 61, 8, 0, 0) == lib.GBSH_EINVAL
+    assert so.gbsh_set_batch_tuning_ex(lib.PREC_MIXED, 15, 8, 8) == lib.GBSH_EINVAL
+    assert so.gbsh_set_batch_tuning_ex(lib.PREC_FP64, 31, 8, 8) == lib.GBSH_EINVAL
+    assert lib.builtin_tuning_entries() >= 0
+
+
+def test_autotune_table_emission():
+    """Tuned sizes become table rows covering N up to the next tuned size; rows equal to the
+    library default are dropped; the emitted C source lists them before the sentinel."""
+    from paper_2010_15595_gb300 import autotune
+    fp, tf = lib.PREC_FP64, lib.PREC_TF
+    res = {(fp, 24): autotune.library_default(fp), (fp, 32): (10, 2, 18), (fp, 40): (12, 1, 16),
+           (tf, 40): (14, 2, 17)}
+    rows = autotune.table_entries(res)
+    assert rows == [(fp, 32, 39, 10, 2, 18), (fp, 40, 60, 12, 1, 16), (tf, 1, 60, 14, 2, 17)]
+    src = autotune.emit_table(rows, [(fp, 1, 30, 12, 6)], "note")
+    assert src.index("{0, 32, 39, 10, 2, 18},") < src.index("{-1, 0, 0, 0, 0, 0},")
+    assert "{0, 1, 30, 12, 6}," in src and "// note" in src

@@ -223,4 +223,4 @@ def test_autotuner_picks_a_candidate_and_keeps_results(gbsh, tmp_path, monkeypat
     after = gbsh.lhaf_batch(mats)
     assert np.array_equal(before, after)  # launch shape never changes the bits
     assert autotune.apply_cache() == 1
-    gbsh.set_batch_tuning(0, 9, 0)
+    gbsh.set_batch_tuning(0, 9, 0, warps_small=0)

@@ -36,8 +36,8 @@ def test_noalloc_matches_workspace_entry_two_calls(gbsh):
     cases = [W.single_lhaf_mid(32), W.single_lhaf_mid(26, seed=3)]
     for A in cases:  # two calls in a row on the shared scratch
         ref, aref, got, agot = _run_both(gbsh, A)
-        _, _, sq = L.lhaf_subset_stats(A)
-        tol = max(1e-9, 512 * U * sq ** 0.5 / abs(ref))  # same gate as the parity tests
+        v, _, sq = L.lhaf_subset_stats(A)
+        tol = max(1e-9, 512 * U * sq ** 0.5 / abs(v))  # same gate as the parity tests
         assert abs(got - ref) <= tol * abs(ref), (A.shape, got, ref)
         assert abs(agot - aref) <= 1e-12 * aref
 
