@@ -290,9 +290,7 @@ template <> struct Cx<tfc> {
     tf_to_dd(v.y, t.im_hi, t.im_lo);
     return t;
   }
-  __device__ __forceinline__ static tfc scale2(tfc v, int s) {
-    return tfc{tf_scale2(v.x, s), tf_scale2(v.y, s)};
-  }
+  __device__ __forceinline__ static tfc scale2(tfc v, int s) { return tfc_scale2(v, s); }
 };
 __device__ __forceinline__ tf3 rfma(tf3 a, tf3 b, tf3 c) { return tf_fma(a, b, c); }
 
@@ -312,10 +310,11 @@ template <> __device__ __forceinline__ tf3 inv_int<tf3>(int k) {
   return tf3(c_inv_tf[k][0], c_inv_tf[k][1], c_inv_tf[k][2]);
 }
 
-// for (i = begin; i < end; i += step) f(i), kept rolled on the triple-float path: a
-// triple-float complex multiply-accumulate is ~220 FP32 instructions, and unrolled copies
-// of loops made of them overflow the instruction cache (the profile showed warps stalled
-// on instruction fetch). The other arithmetic types get the plain loop.
+// for (i = begin; i < end; i += step) f(i), kept rolled on the triple-float path, where
+// code size is what limits speed: the 16 warps of an SM run different phases of the
+// per-subset code at once, and the profile showed them waiting for instructions more than
+// for anything else. Every loop of the per-subset code goes through it. The other
+// arithmetic types get the plain loop.
 template <class T, class F>
 __device__ __forceinline__ void for_rolled(int begin, int end, int step, F&& f) {
   if constexpr (std::is_same<T, tfc>::value) {
@@ -324,6 +323,14 @@ __device__ __forceinline__ void for_rolled(int begin, int end, int step, F&& f) 
   } else {
     for (int i = begin; i < end; i += step) f(i);
   }
+}
+
+// floor(e / d) for 0 <= e < 4096 and 1 <= d <= 64, given inv_d = the FP32 reciprocal of d
+// rounded to nearest: (e + 1/2) inv_d is within (e + 1/2)/d * 2^-23 < 5e-4 of (e + 1/2)/d,
+// whose distance to the nearest integer is at least 1/(2d) >= 1/128, so truncation is exact.
+// Three instructions where an integer division takes about twenty.
+__device__ __forceinline__ int div_small(int e, float inv_d) {
+  return __float2int_rz(__fmul_rn(__int2float_rn(e) + 0.5f, inv_d));
 }
 
 // Compensated (two-sum) accumulator for the signed subset sum.
@@ -371,11 +378,11 @@ __device__ __forceinline__ void column_update(T* __restrict__ H, int ldh, int S,
   const int G = Rr > 1 ? (Rr - 2 + q) / q : 0;  // lanes that can start inside one row
   const bool seg = Rr > 0 && (4 * q + 2 * G + 4 * passes) < passes * (4 * Rr + 4);
   if (!seg) {
-    for (int r = lane; r < S; r += 32) {
+    for_rolled<T>(lane, S, 32, [&](int r) {
       T acc = zero;
       for_rolled<T>(c + 2, S, 1, [&](int i) { acc = cfma(acc, H[r * ldh + i], H[i * ldh + c]); });
       H[r * ldh + c + 1] = cfma(acc, r == c + 1 ? one : piv, H[r * ldh + c + 1]);
-    }
+    });
     return;
   }
   const int e0 = lane * q;
@@ -408,21 +415,21 @@ __device__ __forceinline__ void column_update(T* __restrict__ H, int ldh, int S,
   const int zs = rz - ra;
   T tail = zs == 0 ? a0 : (zs == 1 ? a1 : a2);
   const int ra_key = has ? ra : -1;
-  for (int j = 1; j <= G; ++j) {
+  for_rolled<T>(1, G + 1, 1, [&](int j) {
     const T nb = shfl_down_c(a0, (unsigned)j);
     const int rj = __shfl_down_sync(FULL, ra_key, (unsigned)j);
     if (has && lane + j < 32 && rj == rz) tail = cadd(tail, nb);
-  }
+  });
   // rows owned: ra when the lane starts it, then the following rows that start in range
   const int own1 = (o == 0) ? ra : ra + 1;
-  for (int w = 0; w < passes; ++w) {
+  for_rolled<T>(0, passes, 1, [&](int w) {
     const int r = own1 + w;
     if (has && r <= rz) {
       const int sl = r - ra;
       const T v = (r == rz) ? tail : (sl == 0 ? a0 : (sl == 1 ? a1 : a2));
       H[r * ldh + c + 1] = cfma(v, r == c + 1 ? one : piv, H[r * ldh + c + 1]);
     }
-  }
+  });
 }
 
 // ------------------------------------------------------------------------------------
@@ -460,7 +467,7 @@ __device__ __noinline__ Term subset_term_full(const Problem& P, uint64_t z, int 
   __syncwarp();
 
   // ---- 1b. K' = [[0, v^T], [X v, X A0_Z]]; row r>=1 of the M block is row (r-1+k) mod m
-  for (int e = lane; e < S * S; e += 32) {
+  for_rolled<T>(lane, S * S, 32, [&](int e) {
     int r = e / S, c = e - r * S;
     double2 val;
     if (r == 0) {
@@ -472,10 +479,10 @@ __device__ __noinline__ Term subset_term_full(const Problem& P, uint64_t z, int 
       val = (c == 0) ? __ldg(P.v + rs) : __ldg(P.A0 + (size_t)rs * P.Ne + idx[c - 1]);
     }
     H[r * ldh + c] = Cx<T>::from(val);
-  }
+  });
   // polynomial accumulators: P_0 = 1, P_t = 0
-  for (int e = lane; e < poly_offset(S + 1, D); e += 32)
-    Pl[e] = Cx<T>::make(e == 0 ? R(1) : R(0), R(0));
+  for_rolled<T>(lane, poly_offset(S + 1, D), 32,
+                [&](int e) { Pl[e] = Cx<T>::make(e == 0 ? R(1) : R(0), R(0)); });
   __syncwarp();
 
   // ---- 2. Hessenberg reduction by stabilised elementary similarities (index 0 fixed
@@ -495,10 +502,10 @@ __device__ __noinline__ Term subset_term_full(const Problem& P, uint64_t z, int 
     // pivot: largest magnitude in column c among rows c+1..S-1
     unsigned best = 0u;
     int brow = c + 1;
-    for (int r = c + 1 + lane; r < S; r += 32) {
+    for_rolled<T>(c + 1 + lane, S, 32, [&](int r) {
       unsigned mk = mag_key(H[r * ldh + c]);
       if (mk > best) { best = mk; brow = r; }
-    }
+    });
     unsigned mx = __reduce_max_sync(FULL, best);
     if constexpr (std::is_same<T, tfc>::value) {
       // A column whose candidates are all below 2^-kZeroBits of the column's largest entry
@@ -510,10 +517,10 @@ __device__ __noinline__ Term subset_term_full(const Problem& P, uint64_t z, int 
       // Keys compare FP32 bit patterns, so 2^-64 is 64 << 23 in the key.
       constexpr unsigned kZeroBits = 64u;
       unsigned cm = 0u;
-      for (int r = lane; r <= c; r += 32) {
+      for_rolled<T>(lane, c + 1, 32, [&](int r) {
         const unsigned k2 = mag_key(H[r * ldh + c]);
         cm = k2 > cm ? k2 : cm;
-      }
+      });
       cm = __reduce_max_sync(FULL, cm);
       cm = cm > mx ? cm : mx;
       if (cm >= (kZeroBits << 23) && mx < cm - (kZeroBits << 23)) mx = 0u;
@@ -526,17 +533,17 @@ __device__ __noinline__ Term subset_term_full(const Problem& P, uint64_t z, int 
     unsigned cand = __ballot_sync(FULL, best == mx);
     int p = __shfl_sync(FULL, brow, __ffs(cand) - 1);
     if (p != c + 1) {
-      for (int j = c + lane; j < S; j += 32) {  // swap rows p and c+1 (columns >= c)
+      for_rolled<T>(c + lane, S, 32, [&](int j) {  // swap rows p and c+1 (columns >= c)
         T a = H[p * ldh + j], b = H[(c + 1) * ldh + j];
         H[p * ldh + j] = b;
         H[(c + 1) * ldh + j] = a;
-      }
+      });
       __syncwarp();
-      for (int r = lane; r < S; r += 32) {  // swap columns p and c+1
+      for_rolled<T>(lane, S, 32, [&](int r) {  // swap columns p and c+1
         T a = H[r * ldh + p], b = H[r * ldh + c + 1];
         H[r * ldh + p] = b;
         H[r * ldh + c + 1] = a;
-      }
+      });
       __syncwarp();
     }
     const T piv = H[(c + 1) * ldh + c];
@@ -550,18 +557,20 @@ __device__ __noinline__ Term subset_term_full(const Problem& P, uint64_t z, int 
       // elimination (the diagonal entry itself is unchanged by the similarity) and is
       // parked in the subdiagonal slot H[c+1][c], which is never read again.
       const T rinv = crecip(bp);
-      for (int j = c + 1 + lane; j < S; j += 32) {
+      for_rolled<T>(c + 1 + lane, S, 32, [&](int j) {
         const T u = cmul(H[(c + 1) * ldh + j], rinv);
         H[(c + 1) * ldh + (j == c + 1 ? c : j)] = u;
-      }
+      });
       // multipliers H[r][c] / 2^E, kept in column c below the subdiagonal
-      for (int r = c + 2 + lane; r < S; r += 32) H[r * ldh + c] = Cx<T>::scale2(H[r * ldh + c], -E);
+      for_rolled<T>(c + 2 + lane, S, 32,
+                    [&](int r) { H[r * ldh + c] = Cx<T>::scale2(H[r * ldh + c], -E); });
       __syncwarp();
       // rows r >= c+2:  H[r][j] -= m_r u_j,  j >= c+1
       {
         const int C = Rr + 1;
+        const float inv_c = __frcp_rn((float)C);
         for_rolled<T>(lane, Rr * C, 32, [&](int e) {
-          int rr = e / C, jj = e - rr * C;
+          int rr = div_small(e, inv_c), jj = e - rr * C;
           int r = c + 2 + rr, j = c + 1 + jj;
           const T u = H[(c + 1) * ldh + (jj == 0 ? c : j)];
           H[r * ldh + j] = cfms(H[r * ldh + j], H[r * ldh + c], u);
@@ -597,23 +606,23 @@ __device__ __noinline__ Term subset_term_full(const Problem& P, uint64_t z, int 
   int sig = 0;
   if constexpr (std::is_same<T, tfc>::value) {
     int g = -(1 << 20);
-    for (int e = lane; e < S * S; e += 32) {
+    for_rolled<T>(lane, S * S, 32, [&](int e) {
       const int a = e / S, bb = e - a * S;
-      if (a > bb || mag_key(H[a * ldh + bb]) == 0u) continue;
+      if (a > bb || mag_key(H[a * ldh + bb]) == 0u) return;
       const int len = bb - a + 1;
-      if (a < bb && ((zmask >> a) & ((1ull << (bb - a)) - 1ull)) != 0ull) continue;
+      if (a < bb && ((zmask >> a) & ((1ull << (bb - a)) - 1ull)) != 0ull) return;
       const int eb = pow2_exponent(H[a * ldh + bb]) + 2 + (a < bb ? kexp[bb] - kexp[a] : 0);
       const int q = eb >= 0 ? (eb + len - 1) / len : -((-eb) / len);
       g = q > g ? q : g;
-    }
+    });
     g = __reduce_max_sync(FULL, g);
     sig = g == -(1 << 20) ? 0 : (g > 3 ? 3 - g : (g < -3 ? -3 - g : 0));
   }
-  for (int e = lane; e < S * S; e += 32) {
+  for_rolled<T>(lane, S * S, 32, [&](int e) {
     const int a = e / S, bb = e - a * S;
     if (a < bb) H[a * ldh + bb] = Cx<T>::scale2(H[a * ldh + bb], kexp[bb] - kexp[a] + sig * (bb - a + 1));
     else if (a == bb && sig != 0) H[a * ldh + a] = Cx<T>::scale2(H[a * ldh + a], sig);
-  }
+  });
   __syncwarp();
 
   // ---- 3. La Budde over trailing blocks. With the subdiagonal products folded into the
@@ -631,8 +640,9 @@ __device__ __noinline__ Term subset_term_full(const Problem& P, uint64_t z, int 
     {
       const int nt = S - s;                            // targets t = s+1 .. S
       const int ne = (degs < D - 1 ? degs : D - 1) + 1;
+      const float inv_ne = __frcp_rn((float)ne);
       for_rolled<T>(lane, nt * ne, 32, [&](int f) {
-        const int ti = f / ne, e = f - ti * ne;
+        const int ti = div_small(f, inv_ne), e = f - ti * ne;
         const int t = s + 1 + ti;
         const int d = e + 1 + ti;
         const int a = S - t;
@@ -680,11 +690,11 @@ __device__ __noinline__ Term subset_term_full(const Problem& P, uint64_t z, int 
   }
   // (a) r = qK / qM   (qM_0 = 1)
   T r = qK;
-  for (int s = 0; s < D; ++s) {
+  for_rolled<T>(0, D, 1, [&](int s) {
     T rs = shfl_c(r, s);
     T qs = shfl_up_c(qM, s);
     if (lane > s) r = cfms(r, qs, rs);
-  }
+  });
   // loop terms l_j = -r_{j+1} (for sig != 0: r of the rescaled matrices, whose loop terms
   // carry one factor 2^sig more than the traces of the same degree)
   T lj = shfl_down_c(r, 1);
@@ -692,16 +702,16 @@ __device__ __noinline__ Term subset_term_full(const Problem& P, uint64_t z, int 
   if (sig != 0) lj = Cx<T>::scale2(lj, -sig);
   // (b) power traces t_j = tr(M^j):  t_j = -j q_j - sum_{i=1}^{j-1} q_i t_{j-i}
   T tr = cscale(qM, -(R)lane);
-  for (int s = 1; s < n; ++s) {
+  for_rolled<T>(1, n, 1, [&](int s) {
     T ts = shfl_c(tr, s);
     T qs = shfl_up_c(qM, s);
     if (lane > s) tr = cfms(tr, qs, ts);
-  }
+  });
   // (c) j c_j = (t_j + j l_j) / 2
   const T icj = Cx<T>::make(R(0.5) * rfma((R)lane, lj.x, tr.x), R(0.5) * rfma((R)lane, lj.y, tr.y));
   // (d) exp-polynomial: j p_j = sum_{i=1}^{j} i c_i p_{j-i}, p_0 = 1
   T acc = zero;
-  for (int s = 0; s < n; ++s) {
+  for_rolled<T>(0, n, 1, [&](int s) {
     T ps;
     if (s == 0) {
       ps = Cx<T>::make(R(1), R(0));
@@ -710,7 +720,7 @@ __device__ __noinline__ Term subset_term_full(const Problem& P, uint64_t z, int 
     }
     T ics = shfl_up_c(icj, s);
     if (lane > s) acc = cfma(acc, ics, ps);
-  }
+  });
   T pn = cscale(shfl_c(acc, n), inv_int<R>(n));
   __syncwarp();
   Term out = Cx<T>::to_term(pn);

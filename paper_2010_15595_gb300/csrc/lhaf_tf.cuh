@@ -177,15 +177,18 @@ __device__ __forceinline__ void tf_to_dd(tf3 x, double& hi, double& lo) {
 }
 
 // -------------------------------------------------------------------------- complex
-struct tfc {
+struct alignas(8) tfc {  // 8-byte aligned: shared-memory words move in 64-bit pairs
   tf3 x, y;
 };
 
-__device__ __forceinline__ tfc cadd(tfc p, tfc q) { return tfc{p.x + q.x, p.y + q.y}; }
-// The complex multiply-accumulates are ~220 FP32 instructions each and appear at many
+// The complex operations are tens to hundreds of FP32 instructions each and appear at many
 // places of the per-subset code; compiled out of line, one copy serves every call site, so
-// the instruction footprint of the hot loops stays inside the instruction cache (inlined,
-// the warps spent most of their time waiting for instructions: 1.4x slower at N = 40).
+// the instruction footprint of the per-subset code stays small (warps that run different
+// phases of it share the instruction cache). Inlined multiply-accumulates were 1.4x slower
+// at N = 40; with the add, the real scaling and the power-of-two scaling out of line as
+// well, and every loop of the per-subset code kept rolled (for_rolled), the per-subset
+// function shrank from 70 KB to 43 KB of code and N = 40 ran 9 % faster.
+__device__ __noinline__ tfc cadd(tfc p, tfc q) { return tfc{p.x + q.x, p.y + q.y}; }
 // acc - p*q
 __device__ __noinline__ tfc cfms(tfc acc, tfc p, tfc q) {
   return tfc{tf_dot2(-p.x, q.x, p.y, q.y, acc.x), tf_dot2(-p.x, q.y, -p.y, q.x, acc.y)};
@@ -196,13 +199,15 @@ __device__ __forceinline__ tfc cmul(tfc p, tfc q) {
   const tf3 z(0.0f);
   return cfma(tfc{z, z}, p, q);
 }
-__device__ __forceinline__ tfc cscale(tfc p, tf3 s) { return tfc{p.x * s, p.y * s}; }
+__device__ __noinline__ tfc cscale(tfc p, tf3 s) { return tfc{p.x * s, p.y * s}; }
 // out of line as well: ~450 instructions once per elimination step (2 % faster at N = 40)
 __device__ __noinline__ tfc crecip(tfc p) {
   const tf3 d = tf_dot2(p.x, p.x, p.y, p.y, tf3(0.0f));
   const tf3 r = tf_recip(d);
   return tfc{p.x * r, -(p.y * r)};
 }
+// exact power-of-two scaling of both parts, out of line like the operations above
+__device__ __noinline__ tfc tfc_scale2(tfc v, int s) { return tfc{tf_scale2(v.x, s), tf_scale2(v.y, s)}; }
 __device__ __forceinline__ int pow2_exponent(tfc p) {
   const unsigned ex = (__float_as_uint(p.x.a) >> 23) & 0xffu;
   const unsigned ey = (__float_as_uint(p.y.a) >> 23) & 0xffu;
