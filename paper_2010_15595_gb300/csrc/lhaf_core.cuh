@@ -688,25 +688,45 @@ __device__ __noinline__ Term subset_term_full(const Problem& P, uint64_t z, int 
       sig += sig2;
     }
   }
-  // (a) r = qK / qM   (qM_0 = 1)
-  T r = qK;
-  for_rolled<T>(0, D, 1, [&](int s) {
-    T rs = shfl_c(r, s);
-    T qs = shfl_up_c(qM, s);
-    if (lane > s) r = cfms(r, qs, rs);
-  });
+  // (a) r = qK / qM   (qM_0 = 1), coefficients 0..D
+  // (b) power traces t_j = tr(M^j):  t_j = -j q_j - sum_{i=1}^{j-1} q_i t_{j-i}, j = 1..n
+  // Both are recursions over s in which coefficient s, once final, updates every higher
+  // one. When the D+1 + n coefficients fit the warp (n <= 15) they share one loop: lanes
+  // 0..D hold r, lanes D+1..D+n hold t_1..t_n, and one multiply-add per step serves both
+  // (the same operations on the same operands as two separate loops).
+  T r, tr;
+  if (D + 1 + n <= 32) {
+    const bool inB = lane > D;
+    const int j = inB ? lane - D : lane;
+    const T qj = shfl_c(qM, j <= D ? j : 0);
+    T v = inB ? cscale(qj, -(R)j) : qK;
+    for_rolled<T>(0, D, 1, [&](int s) {
+      const T vs = shfl_c(v, inB ? D + s : s);
+      const T qs = shfl_c(qM, j > s ? j - s : 0);
+      const bool act = inB ? (s >= 1 && s < n && j > s) : (j > s);
+      if (act) v = cfms(v, qs, vs);
+    });
+    r = v;
+    tr = shfl_c(v, D + lane <= 31 ? D + lane : 31);  // t_lane on lanes 1..n
+  } else {
+    r = qK;
+    for_rolled<T>(0, D, 1, [&](int s) {
+      T rs = shfl_c(r, s);
+      T qs = shfl_up_c(qM, s);
+      if (lane > s) r = cfms(r, qs, rs);
+    });
+    tr = cscale(qM, -(R)lane);
+    for_rolled<T>(1, n, 1, [&](int s) {
+      T ts = shfl_c(tr, s);
+      T qs = shfl_up_c(qM, s);
+      if (lane > s) tr = cfms(tr, qs, ts);
+    });
+  }
   // loop terms l_j = -r_{j+1} (for sig != 0: r of the rescaled matrices, whose loop terms
   // carry one factor 2^sig more than the traces of the same degree)
   T lj = shfl_down_c(r, 1);
   lj = Cx<T>::make(-lj.x, -lj.y);
   if (sig != 0) lj = Cx<T>::scale2(lj, -sig);
-  // (b) power traces t_j = tr(M^j):  t_j = -j q_j - sum_{i=1}^{j-1} q_i t_{j-i}
-  T tr = cscale(qM, -(R)lane);
-  for_rolled<T>(1, n, 1, [&](int s) {
-    T ts = shfl_c(tr, s);
-    T qs = shfl_up_c(qM, s);
-    if (lane > s) tr = cfms(tr, qs, ts);
-  });
   // (c) j c_j = (t_j + j l_j) / 2
   const T icj = Cx<T>::make(R(0.5) * rfma((R)lane, lj.x, tr.x), R(0.5) * rfma((R)lane, lj.y, tr.y));
   // (d) exp-polynomial: j p_j = sum_{i=1}^{j} i c_i p_{j-i}, p_0 = 1
