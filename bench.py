@@ -158,10 +158,11 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(N: int, path: str):
-    """DRAM bytes of one evaluation on `path` ("tf" or "fp64"): every launch of the evaluation
-    (expansion, the popcount-class launches of the subset kernel, the two finalize levels),
-    from the committed ncu summary, if it was taken on the current kernel sources; else None."""
+def recorded_traffic(N: int, path: str, whole: bool = False):
+    """DRAM bytes per evaluation on `path` ("tf" or "fp64") from the committed ncu summary, if
+    it was taken on the current kernel sources (else None): the subset kernel's class launches
+    (the dominant kernel), or with whole=True every launch of the evaluation (expansion,
+    class launches, the two finalize levels)."""
     p = os.path.join(ROOT, "profiles", "lhaf_subsets_dram_traffic.json")
     try:
         with open(p) as f:
@@ -170,7 +171,8 @@ def recorded_traffic(N: int, path: str):
         return None
     if rec.get("kernel_source_hash") != kernel_source_hash():
         return None
-    return rec.get("bytes_per_evaluation", {}).get(path, {}).get(str(N))
+    key = "bytes_per_evaluation" if whole else "subset_kernel_bytes_per_evaluation"
+    return rec.get(key, {}).get(path, {}).get(str(N))
 
 
 def recorded_probes() -> dict:
@@ -307,6 +309,7 @@ def run_ours(args, rank, world, local_rank):
             "ms_per_step": fp_run["total_s"] * 1e3 / args.steps,
             "roofline": {"bound": "alu", "achieved": fp_ach, "peak": fp_peak, "unit": "TFLOP/s",
                          "frac": fp_ach / fp_peak, "traffic": recorded_traffic(N, "fp64"),
+                         "traffic_whole_evaluation": recorded_traffic(N, "fp64", whole=True),
                          "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
                          "measured_dfma_probe_tflops": probes.get("dfma_tflops"),
                          "kernel": "lhaf_subsets_kernel<double2>",
@@ -463,6 +466,10 @@ def run_ours(args, rank, world, local_rank):
             "roofline": {"bound": "alu", "achieved": tf_ach, "peak": tf_peak,
                          "unit": "T FP32 instr/s", "frac": tf_ach / tf_peak,
                          "traffic": recorded_traffic(N, "tf"),
+                         "traffic_whole_evaluation": recorded_traffic(N, "tf", whole=True),
+                         "traffic_note": "DRAM bytes per evaluation (ncu): the subset kernel's "
+                                         "class launches; the whole evaluation adds the chunk "
+                                         "partial sums, L2-resident in the timed run",
                          "peak_source": "derived: 152 SM x 128 FP32 lanes/clk x 2.07 GHz",
                          "measured_ffma_probe_t_instr": probes.get("ffma_t_instr"),
                          "kernel": "lhaf_subsets_kernel<tfc> (+expand, finalize in the step time)",
