@@ -570,15 +570,18 @@ def run_serving_workload(args):
     input modes (mean ~20 photons), output displacement ~CN(0, 0.1^2), Fock cutoff 4, loop
     hafnians up to N=36. Plain path (one single-evaluation launch sequence and one
     synchronisation per loop hafnian, one sample at a time) vs the served path (continuous
-    batching); Poisson arrivals at 0.5, 1, 2 and 3 times the plain throughput; latencies from
+    batching, loop hafnians above --serve-tick-subsets subsets split into subset ranges over
+    ticks); Poisson arrivals at 0.5, 1, 2 and 3 times the plain throughput; latencies from
     submission to completion, with n per rate; the fraction of samples that dropped a
-    candidate above the N <= 36 cap."""
+    candidate above the N <= 36 cap. --serve-compare also runs the served path without
+    splitting and the plain path under the same Poisson arrivals."""
     import numpy as np
     from paper_2010_15595_gb300 import sampler as S, workloads
     U, r, alpha = workloads.serving_state()
     st = S.pure_state(U, r, alpha)
     res = {"workload": "chain-rule GBS sampler, M=100, r=0.8 on 25 modes, alpha~CN(0,0.1^2), "
-                       "cutoff 4, N<=36 (candidates above are dropped and counted)"}
+                       "cutoff 4, N<=36 (candidates above are dropped and counted)",
+           "tick_subsets": args.serve_tick_subsets}
 
     def run_batch(smp, seeds):
         t = time.perf_counter()
@@ -586,49 +589,54 @@ def run_serving_workload(args):
         out = [smp.wait(rr, timeout=1800) for rr in rids]
         return time.perf_counter() - t, out
 
+    def poisson(smp, mult, plain_rate):
+        lam = mult * plain_rate
+        gaps = np.random.default_rng(2 + int(mult * 10)).exponential(1.0 / lam, args.serve_poisson)
+        t0 = time.perf_counter()
+        rids = []
+        for i, gap in enumerate(gaps):
+            target = t0 + gaps[: i + 1].sum()
+            now = time.perf_counter()
+            if target > now:
+                time.sleep(target - now)
+            rids.append(smp.submit(5000 + 1000 * int(mult * 10) + i))
+        outs = [smp.wait(rr, timeout=1800) for rr in rids]
+        span = time.perf_counter() - t0
+        lats = np.array([o[1]["latency_s"] for o in outs])
+        return {"rate_x_plain": mult, "arrival_per_s": lam, "requests": len(outs),
+                "samples_per_s": len(outs) / span, "p50_s": float(np.median(lats)),
+                "p99_s": float(np.quantile(lats, 0.99)), "max_s": float(lats.max())}
+
     with S.Sampler(st, cutoff=4, n_cap=36, batching=False) as plain:
         dt, out = run_batch(plain, range(args.serve_plain))
-    plain_rate = args.serve_plain / dt
+        plain_rate = args.serve_plain / dt
+        if args.serve_compare:
+            res["plain_poisson"] = [poisson(plain, m, plain_rate) for m in args.serve_rates]
     lat = np.array([o[1]["latency_s"] for o in out])
     res["plain"] = {"samples": args.serve_plain, "samples_per_s": plain_rate,
                     "mean_photons": float(np.mean([o[0].sum() for o in out])),
                     "per_sample_s_p50": float(np.median(np.diff(np.sort(lat), prepend=0.0))),
                     "note": "all submitted at t=0 (saturated), served one at a time"}
-    with S.Sampler(st, cutoff=4, n_cap=36, max_active=args.serve_slots) as smp:
-        dt, out = run_batch(smp, range(1000, 1000 + args.serve_saturated))
-        capped = sum(1 for o in out if o[1]["truncated"] > 0)
-        res["served_saturated"] = {"samples": args.serve_saturated,
-                                   "samples_per_s": args.serve_saturated / dt,
-                                   "truncated_steps": int(sum(o[1]["truncated"] for o in out)),
-                                   "samples_with_capped_candidate": capped,
-                                   "capped_fraction": capped / args.serve_saturated,
-                                   "slots": args.serve_slots}
-        rng = np.random.default_rng(2)
-        res["poisson"] = []
-        for mult in args.serve_rates:
-            lam = mult * plain_rate
-            gaps = rng.exponential(1.0 / lam, args.serve_poisson)
-            t0 = time.perf_counter()
-            rids = []
-            for i, gap in enumerate(gaps):
-                target = t0 + gaps[: i + 1].sum()
-                now = time.perf_counter()
-                if target > now:
-                    time.sleep(target - now)
-                rids.append(smp.submit(5000 + 1000 * int(mult * 10) + i))
-            outs = [smp.wait(rr, timeout=1800) for rr in rids]
-            span = time.perf_counter() - t0
-            lats = np.array([o[1]["latency_s"] for o in outs])
-            res["poisson"].append({"rate_x_plain": mult, "arrival_per_s": lam,
-                                   "requests": len(outs), "samples_per_s": len(outs) / span,
-                                   "p50_s": float(np.median(lats)),
-                                   "p99_s": float(np.quantile(lats, 0.99)),
-                                   "max_s": float(lats.max())})
+    configs = [("", args.serve_tick_subsets)]
+    if args.serve_compare and args.serve_tick_subsets:
+        configs.append(("_unsplit", 0))
+    for suffix, ts in configs:
+        with S.Sampler(st, cutoff=4, n_cap=36, max_active=args.serve_slots,
+                       tick_subsets=ts) as smp:
+            dt, out = run_batch(smp, range(1000, 1000 + args.serve_saturated))
+            capped = sum(1 for o in out if o[1]["truncated"] > 0)
+            res["served_saturated" + suffix] = {
+                "samples": args.serve_saturated, "samples_per_s": args.serve_saturated / dt,
+                "truncated_steps": int(sum(o[1]["truncated"] for o in out)),
+                "samples_with_capped_candidate": capped,
+                "capped_fraction": capped / args.serve_saturated, "slots": args.serve_slots,
+                "tick_subsets": ts}
+            res["poisson" + suffix] = [poisson(smp, m, plain_rate) for m in args.serve_rates]
     # the plain path under the same arrivals: a queue in front of a single server
     res["plain_queue_model"] = []
     for mult in args.serve_rates:
         lam = mult * plain_rate
-        gaps = np.random.default_rng(2).exponential(1.0 / lam, args.serve_poisson)
+        gaps = np.random.default_rng(2 + int(mult * 10)).exponential(1.0 / lam, args.serve_poisson)
         svc = np.random.default_rng(3).choice(np.diff(np.sort(lat), prepend=0.0), args.serve_poisson)
         arr = np.cumsum(gaps)
         done = np.zeros_like(arr)
@@ -817,6 +825,10 @@ def main(argv=None):
     p.add_argument("--serve-poisson", type=int, default=60,
                    help="requests per arrival rate (the committed serving profile uses 200)")
     p.add_argument("--serve-rates", type=float, nargs="+", default=[0.5, 1.0, 2.0, 3.0])
+    p.add_argument("--serve-tick-subsets", type=int, default=1 << 16,
+                   help="split loop hafnians above this many subsets over ticks (0: off)")
+    p.add_argument("--serve-compare", action="store_true",
+                   help="also serve without splitting and run the plain path under Poisson arrivals")
     p.add_argument("--fig1", action="store_true",
                    help="run the Fig. 1 TVD experiment (Sec. III) instead of the benchmark")
     p.add_argument("--fig1-samples", type=int, default=200000)

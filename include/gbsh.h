@@ -372,6 +372,15 @@ typedef struct {
   const double* mean;           /* 2M host: quadrature means R-bar */
   const double* w_factor;       /* 2M x 2M host row-major: W = w_factor w_factor^T */
   const gbsh_c128* fill_map;    /* M x 2M host row-major complex */
+  /* Split evaluation (batching = 1, GBSH_PREC_FP64): 0 evaluates every loop hafnian of a
+   * tick in the tick's batched launch. T > 0 (rounded down to a power of two, at least
+   * 64) evaluates a loop hafnian with more than T pair subsets in fixed ranges of T
+   * enumeration indices, spread over ticks: each tick runs at most max(T, the subsets of
+   * its batched launch) subsets of such ranges, oldest chains first, and a chain draws its
+   * next photon number once all its candidates are done. This bounds the time of a tick,
+   * so chains with small loop hafnians are not held up by ones with large ones. The
+   * ranges depend only on the size and T, so samples stay the same alone and in any mix. */
+  size_t tick_subsets;
 } gbsh_sampler_cfg;
 
 typedef struct {
@@ -424,7 +433,8 @@ int gbsh_philox4x32(const uint32_t counter[4], const uint32_t key[2], uint32_t o
  * Sharing: all calls share the one array, which keeps the last call's contents (the call
  * clears what must start at zero). Calls whose GPU work may overlap -- on different
  * streams, or from different threads without ordering -- race on it; serialise them.
- * The launch plan is the library default (gbsh_set_lhaf_tuning does not apply), except
+ * The launch plan is the tuning table's entry for N (gbsh_set_lhaf_tuning's process-wide
+ * override does not apply), except
  * that for large N the number of subset chunks is halved until the chunk partial sums fit
  * the array; the result then agrees with gbsh_lhaf's to rounding, not bit for bit.
  * Errors: GBSH_EINVAL (N < 0, N > GBSH_MAX_N, lda < N, NULL pointers); GBSH_ENOMEM if an

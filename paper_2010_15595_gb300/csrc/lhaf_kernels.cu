@@ -564,9 +564,9 @@ static cudaError_t launch_classes(const LhafPlan& plan, void* ws, unsigned* visi
 
 // Subsets of the enumeration indices [i_begin, i_end) (z = i ^ (i >> 1)), in chunks of the
 // plan's chunk size starting at i_begin, then the two-level fixed-order finalize.
-static cudaError_t launch_range(const LhafPlan& plan, const double2* base, int ld,
-                                const double2* diag, const int* idx, void* ws,
-                                cudaStream_t stream, uint64_t i_begin, uint64_t i_end) {
+cudaError_t launch_range(const LhafPlan& plan, const double2* base, int ld,
+                         const double2* diag, const int* idx, void* ws,
+                         cudaStream_t stream, uint64_t i_begin, uint64_t i_end) {
   cudaError_t e = launch_expand(plan, base, ld, diag, idx, ws, stream);
   if (e != cudaSuccess) return e;
   const uint64_t span = i_end > i_begin ? i_end - i_begin : 0;

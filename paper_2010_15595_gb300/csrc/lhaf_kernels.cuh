@@ -59,6 +59,12 @@ bool make_tuned_plan(int N, const DeviceInfo& dev, int prec, LhafPlan* plan,
 cudaError_t launch_lhaf(const LhafPlan& plan, const double2* base, int ld, const double2* diag,
                         const int* idx, void* ws, cudaStream_t stream);
 
+// launch_lhaf restricted to the enumeration indices [i_begin, i_end) (expansion from `base`,
+// `diag`, `idx` as in launch_lhaf); the range's compensated partial as for launch_lhaf_range.
+cudaError_t launch_range(const LhafPlan& plan, const double2* base, int ld, const double2* diag,
+                         const int* idx, void* ws, cudaStream_t stream, uint64_t i_begin,
+                         uint64_t i_end);
+
 // The subsets of the enumeration indices [i_begin, i_end) only (z = i ^ (i >> 1); any
 // partition of [0, 2^n) into such ranges covers every subset once). Writes the range's
 // compensated partial (re_hi, re_lo, im_hi, im_lo, sum |p_Z|) to ws + off_out + 3 doubles.

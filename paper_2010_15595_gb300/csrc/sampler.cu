@@ -19,9 +19,13 @@
 // chain by one mode: one kernel forms the fill vectors gamma^(k) of all chains, and one
 // batched launch evaluates all (chain, s_k) loop hafnians together. Chains are admitted as
 // slots and device memory allow, so requests that arrive while others are on the GPU join
-// the next tick (continuous batching). All randomness of a chain is drawn from a
-// counter-based generator keyed by the request seed, and a loop hafnian's value does not
-// depend on the batch it runs in, so a sample is the same alone and in any mix.
+// the next tick (continuous batching). With split evaluation on (tick_subsets), loop
+// hafnians above that many subsets run instead as fixed subset ranges spread over ticks
+// (like chunked prefill in LLM serving), so one chain's large loop hafnians do not set the
+// pace of every other chain; such a chain advances when its last range is done. All
+// randomness of a chain is drawn from a counter-based generator keyed by the request seed,
+// and a loop hafnian's value does not depend on the batch or ticks it runs in, so a sample
+// is the same alone and in any mix.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -144,6 +148,14 @@ struct Request {
   int lhafs = 0, ticks = 0, truncated = 0;
 };
 
+// A loop hafnian evaluated in fixed subset ranges over several ticks; `acc` is the
+// compensated partial (re_hi, re_lo, im_hi, im_lo, sum |p_Z|) of the ranges done so far.
+struct SplitCand {
+  int s = 0, N = 0;
+  uint64_t next = 0, total = 0;
+  double acc[5] = {0, 0, 0, 0, 0};
+};
+
 struct Chain {
   std::shared_ptr<Request> req;
   uint32_t chain_no = 0;
@@ -152,7 +164,31 @@ struct Chain {
   int slot = -1;
   std::vector<int> s;
   size_t mem = 0;
+  // mode k's candidates while they are evaluated (split ones may take several ticks)
+  bool open = false;
+  bool trunc = false;
+  int ncand = 0;
+  std::vector<double> val;        // (re, im) of candidate s = 0..ncand-1
+  std::vector<SplitCand> split;   // the split candidates, in increasing s
 };
+
+// Adds a range's compensated partial to an accumulated one (fixed order: ranges are added in
+// increasing index order, so the result does not depend on the ticks they ran in).
+void acc_add(double* acc, const double* p) {
+  auto two_sum = [](double a, double b, double& sm, double& e) {
+    sm = a + b;
+    const double bb = sm - a;
+    e = (a - (sm - bb)) + (b - bb);
+  };
+  double sm, e;
+  two_sum(acc[0], p[0], sm, e);
+  acc[0] = sm;
+  acc[1] += e + p[1];
+  two_sum(acc[2], p[2], sm, e);
+  acc[2] = sm;
+  acc[3] += e + p[3];
+  acc[4] += p[4];
+}
 
 }  // namespace
 
@@ -180,12 +216,16 @@ struct gbsh_sampler {
   size_t idx_cap = 0;
   void* ws = nullptr;
   size_t ws_bytes = 0;
+  double* dpart = nullptr;  // range partials of one tick (5 doubles each)
+  size_t part_cap = 0;
   std::vector<int> free_slots;
 
   void run();
   int tick(std::vector<Chain>& active);
   int ensure_ws(size_t bytes);
   int ensure_idx(size_t n);
+  int ensure_part(size_t n);
+  uint64_t split_size() const;
   size_t chain_mem_estimate(int nphot) const;
 };
 
@@ -222,6 +262,26 @@ int gbsh_sampler::ensure_ws(size_t bytes) {
   return GBSH_OK;
 }
 
+int gbsh_sampler::ensure_part(size_t n) {
+  if (n <= part_cap) return GBSH_OK;
+  if (dpart) cudaFree(dpart);
+  dpart = nullptr;
+  part_cap = 0;
+  const size_t want = std::max(n, (size_t)64);
+  cudaError_t e = cudaMalloc(&dpart, sizeof(double) * 5 * want);
+  if (e != cudaSuccess) return from_cuda(e);
+  part_cap = want;
+  return GBSH_OK;
+}
+
+// Subset-range length of split evaluation (a power of two >= 64), 0 when disabled.
+uint64_t gbsh_sampler::split_size() const {
+  if (!cfg.batching || cfg.precision != GBSH_PREC_FP64 || cfg.tick_subsets == 0) return 0;
+  uint64_t t = 64;
+  while (t * 2 <= (uint64_t)cfg.tick_subsets && t < ((uint64_t)1 << 40)) t *= 2;
+  return t;
+}
+
 int gbsh_sampler::ensure_idx(size_t n) {
   if (n <= idx_cap) return GBSH_OK;
   if (didx) cudaFree(didx);
@@ -233,11 +293,14 @@ int gbsh_sampler::ensure_idx(size_t n) {
   return GBSH_OK;
 }
 
-// Advances every chain in `active` by one mode. Returns a status code.
+// Advances every chain in `active` whose candidates complete in this tick by one mode (with
+// split evaluation off, every chain). Returns a status code.
 int gbsh_sampler::tick(std::vector<Chain>& active) {
   const int M = cfg.M, d = cfg.cutoff;
   const int nch = (int)active.size();
-  // fill vectors gamma^(k) of all chains
+  const uint64_t R = split_size();
+  // fill vectors gamma^(k) of all chains (a chain whose mode is still open gets the same
+  // vector again)
   std::vector<int> slots(nch), ks(nch);
   for (int c = 0; c < nch; ++c) {
     slots[c] = active[c].slot;
@@ -251,24 +314,56 @@ int gbsh_sampler::tick(std::vector<Chain>& active) {
   e = cudaGetLastError();
   if (e != cudaSuccess) return from_cuda(e);
 
-  // candidate loop hafnians (chain c, s_k = s); index lists: mode i repeated s_i times
+  // Open the mode of every chain that has none open: candidates s_k = 0..d with their index
+  // lists (mode i repeated s_i times). Candidates with more than R subsets are split; the
+  // others go into this tick's batched launch. Index lists of split candidates are listed
+  // again every tick while they have ranges left.
   struct Cand { int chain, s, N; size_t idx_off; };
-  std::vector<Cand> cands;
+  std::vector<Cand> cands;                   // batched
+  std::vector<std::pair<int, int>> splits;   // (chain, split index) with ranges left
+  std::vector<size_t> split_idx;             // their index-list offsets
   std::vector<int> idx;
-  std::vector<char> trunc(nch, 0);
+  auto push_list = [&](const Chain& ch, int s) {
+    const size_t off = idx.size();
+    for (int i = 0; i < ch.k; ++i)
+      for (int r = 0; r < ch.s[i]; ++r) idx.push_back(i);
+    for (int r = 0; r < s; ++r) idx.push_back(ch.k);
+    return off;
+  };
+  uint64_t batch_subsets = 0;
   for (int c = 0; c < nch; ++c) {
-    const Chain& ch = active[c];
-    for (int s = 0; s <= d; ++s) {
-      const int N = ch.nphot + s;
-      if (N > cfg.n_cap) {
-        trunc[c] = 1;
-        break;
+    Chain& ch = active[c];
+    if (!ch.open) {
+      ch.open = true;
+      ch.trunc = false;
+      ch.ncand = 0;
+      ch.split.clear();
+      for (int s = 0; s <= d; ++s) {
+        const int N = ch.nphot + s;
+        if (N > cfg.n_cap) {
+          ch.trunc = true;
+          break;
+        }
+        const int n = (N + (N & 1)) / 2;
+        if (R > 0 && ((uint64_t)1 << n) > R) {
+          SplitCand sc;
+          sc.s = s;
+          sc.N = N;
+          sc.total = (uint64_t)1 << n;
+          ch.split.push_back(sc);
+        } else {
+          cands.push_back(Cand{c, s, N, push_list(ch, s)});
+          batch_subsets += (uint64_t)1 << n;
+        }
+        ch.ncand += 1;
       }
-      cands.push_back(Cand{c, s, N, idx.size()});
-      for (int i = 0; i < ch.k; ++i)
-        for (int r = 0; r < ch.s[i]; ++r) idx.push_back(i);
-      for (int r = 0; r < s; ++r) idx.push_back(ch.k);
+      ch.val.assign(2 * (size_t)ch.ncand, 0.0);
     }
+    for (int j = 0; j < (int)ch.split.size(); ++j)
+      if (ch.split[j].next < ch.split[j].total) {
+        splits.emplace_back(c, j);
+        split_idx.push_back(push_list(ch, ch.split[j].s));
+      }
   }
   int rc = ensure_idx(idx.size() + 1);
   if (rc != GBSH_OK) return rc;
@@ -276,6 +371,7 @@ int gbsh_sampler::tick(std::vector<Chain>& active) {
     e = cudaMemcpyAsync(didx, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return from_cuda(e);
   }
+
   const int nc = (int)cands.size();
   std::vector<double> out3(3 * (size_t)nc);
   std::vector<int> Ns(nc);
@@ -286,11 +382,13 @@ int gbsh_sampler::tick(std::vector<Chain>& active) {
                              didx + cands[q].idx_off, M, cands[q].N};
   }
   if (cfg.batching) {
-    gbsh::BatchLayout L = gbsh::batch_layout(Ns.data(), nc, 0);
-    rc = ensure_ws(L.bytes);
-    if (rc != GBSH_OK) return rc;
-    e = gbsh::batch_run(L, in, nc, cfg.precision, 0, ws, st, out3.data());
-    if (e != cudaSuccess) return from_cuda(e);
+    if (nc > 0) {
+      gbsh::BatchLayout L = gbsh::batch_layout(Ns.data(), nc, 0);
+      rc = ensure_ws(L.bytes);
+      if (rc != GBSH_OK) return rc;
+      e = gbsh::batch_run(L, in, nc, cfg.precision, 0, ws, st, out3.data());
+      if (e != cudaSuccess) return from_cuda(e);
+    }
   } else {
     // plain path: one single-evaluation launch sequence (expansion of B, the fill vector and
     // the pattern on the device, the popcount-class launches, finalize) and one
@@ -331,29 +429,90 @@ int gbsh_sampler::tick(std::vector<Chain>& active) {
       if (e != cudaSuccess) return from_cuda(e);
     }
   }
-  // step 5: draw s_k from the normalised weights |lhaf|^2 / s!
+  for (int q = 0; q < nc; ++q) {
+    Chain& ch = active[cands[q].chain];
+    ch.val[2 * (size_t)cands[q].s] = out3[3 * (size_t)q];
+    ch.val[2 * (size_t)cands[q].s + 1] = out3[3 * (size_t)q + 1];
+  }
+
+  // Split candidates: ranges of R enumeration indices, oldest chains first, at most
+  // max(R, batched subsets) subsets in this tick (at least one range).
+  if (!splits.empty()) {
+    gbsh::DeviceInfo dev;
+    e = gbsh::device_info(&dev);
+    if (e != cudaSuccess) return from_cuda(e);
+    e = gbsh::ensure_constants();
+    if (e != cudaSuccess) return from_cuda(e);
+    const uint64_t budget = std::max<uint64_t>(R, batch_subsets);
+    // choose the ranges first, so the workspace and the partial array are sized before the
+    // first launch (neither may be reallocated under queued work)
+    struct Ran { int chain, j; size_t q; uint64_t i0, i1; };
+    std::vector<Ran> ran;
+    std::vector<gbsh::LhafPlan> plans(splits.size());
+    size_t ws_need = 0;
+    uint64_t used = 0;
+    for (size_t q = 0; q < splits.size() && used < budget; ++q) {
+      const SplitCand& sc = active[splits[q].first].split[splits[q].second];
+      if (!gbsh::make_tuned_plan(sc.N, dev, gbsh::kPrecFP64, &plans[q])) return GBSH_EINVAL;
+      ws_need = std::max(ws_need, plans[q].bytes);
+      for (uint64_t i0 = sc.next; i0 < sc.total && used < budget;) {
+        const uint64_t i1 = std::min(i0 + R, sc.total);
+        ran.push_back(Ran{splits[q].first, splits[q].second, q, i0, i1});
+        used += i1 - i0;
+        i0 = i1;
+      }
+    }
+    rc = ensure_ws(ws_need);
+    if (rc == GBSH_OK) rc = ensure_part(ran.size());
+    if (rc != GBSH_OK) return rc;
+    for (size_t r = 0; r < ran.size(); ++r) {
+      const Ran& x = ran[r];
+      const gbsh::LhafPlan& plan = plans[x.q];
+      e = gbsh::launch_range(plan, dB, M, dgam + (size_t)active[x.chain].slot * M,
+                             didx + split_idx[x.q], ws, st, x.i0, x.i1);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dpart + 5 * r, static_cast<char*>(ws) + plan.off_out + 3 * sizeof(double),
+                            5 * sizeof(double), cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) return from_cuda(e);
+      active[x.chain].split[x.j].next = x.i1;
+    }
+    std::vector<double> parts(5 * ran.size());
+    e = cudaMemcpyAsync(parts.data(), dpart, sizeof(double) * parts.size(), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return from_cuda(e);
+    for (size_t r = 0; r < ran.size(); ++r) {  // launch order = index order per candidate
+      Chain& ch = active[ran[r].chain];
+      SplitCand& sc = ch.split[ran[r].j];
+      acc_add(sc.acc, &parts[5 * r]);
+      if (ran[r].i1 == sc.total) {  // its last range
+        ch.val[2 * (size_t)sc.s] = sc.acc[0] + sc.acc[1];
+        ch.val[2 * (size_t)sc.s + 1] = sc.acc[2] + sc.acc[3];
+      }
+    }
+  }
+
+  // step 5: every chain whose candidates are all done draws s_k from the normalised
+  // weights |lhaf|^2 / s!
   std::vector<double> w((size_t)d + 1);
-  size_t q = 0;
   for (int c = 0; c < nch; ++c) {
     Chain& ch = active[c];
+    bool ready = ch.open;
+    for (const SplitCand& sc : ch.split) ready = ready && sc.next == sc.total;
+    if (!ready) continue;
     std::fill(w.begin(), w.end(), 0.0);
     double total = 0.0, fact = 1.0;
-    int ncand = 0;
-    while (q < cands.size() && cands[q].chain == c) {
-      const int s = cands[q].s;
+    for (int s = 0; s < ch.ncand; ++s) {
       if (s > 1) fact *= (double)s;
-      const double re = out3[3 * q], im = out3[3 * q + 1];
+      const double re = ch.val[2 * (size_t)s], im = ch.val[2 * (size_t)s + 1];
       w[s] = (re * re + im * im) / fact;
       total += w[s];
-      ++ncand;
-      ++q;
     }
     const double u = chain_uniform(ch.req->seed, ch.chain_no, (uint32_t)ch.k);
     int sk = 0;
     if (total > 0.0) {
       double cum = 0.0;
-      sk = ncand - 1;
-      for (int s = 0; s < ncand; ++s) {
+      sk = ch.ncand - 1;
+      for (int s = 0; s < ch.ncand; ++s) {
         cum += w[s] / total;
         if (cum > u) {
           sk = s;
@@ -364,8 +523,9 @@ int gbsh_sampler::tick(std::vector<Chain>& active) {
     ch.s[ch.k] = sk;
     ch.nphot += sk;
     ch.k += 1;
-    ch.req->lhafs += ncand;
-    if (trunc[c]) ch.req->truncated += 1;
+    ch.req->lhafs += ch.ncand;
+    if (ch.trunc) ch.req->truncated += 1;
+    ch.open = false;
   }
   return GBSH_OK;
 }
@@ -683,6 +843,7 @@ int gbsh_sampler_destroy(gbsh_sampler* h) {
   cudaFree(h->dslot);
   cudaFree(h->dk);
   cudaFree(h->didx);
+  cudaFree(h->dpart);
   cudaFree(h->ws);
   if (h->st) cudaStreamDestroy(h->st);
   cudaSetDevice(prev);

@@ -170,7 +170,8 @@ class _Cfg(ctypes.Structure):
                 ("max_active", ctypes.c_int), ("mem_budget", ctypes.c_size_t),
                 ("batching", ctypes.c_int), ("precision", ctypes.c_int), ("device", ctypes.c_int),
                 ("threshold", ctypes.c_int), ("mixed", ctypes.c_int), ("mean", ctypes.c_void_p),
-                ("w_factor", ctypes.c_void_p), ("fill_map", ctypes.c_void_p)]
+                ("w_factor", ctypes.c_void_p), ("fill_map", ctypes.c_void_p),
+                ("tick_subsets", ctypes.c_size_t)]
 
 
 class ReqStats(ctypes.Structure):
@@ -217,7 +218,10 @@ class Sampler:
 
     def __init__(self, state, cutoff: int = 4, n_cap: int = 36, max_active: int = 256,
                  mem_budget: int = 2 << 30, batching: bool = True,
-                 precision: int = _lib.PREC_FP64, device: int = 0, threshold: bool = False):
+                 precision: int = _lib.PREC_FP64, device: int = 0, threshold: bool = False,
+                 tick_subsets: int = 0):
+        """tick_subsets > 0 splits loop hafnians with more pair subsets than that into fixed
+        subset ranges evaluated over several ticks (bounded tick time; see gbsh_sampler_cfg)."""
         self.so = _bind()
         self.M = state.B.shape[0]
         M = self.M
@@ -241,7 +245,7 @@ class Sampler:
                    device, 1 if threshold else 0, 1 if mixed else 0,
                    self._mean.ctypes.data if mixed else None,
                    self._wf.ctypes.data if mixed else None,
-                   self._fm.ctypes.data if mixed else None)
+                   self._fm.ctypes.data if mixed else None, int(tick_subsets))
         h = ctypes.c_void_p()
         _lib._check(self.so.gbsh_sampler_create(ctypes.byref(cfg), ctypes.byref(h)),
                     "gbsh_sampler_create")

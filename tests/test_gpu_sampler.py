@@ -74,6 +74,33 @@ def test_same_alone_and_in_mix_and_plain():
         assert np.array_equal(a, b)
 
 
+def test_split_evaluation_same_samples():
+    """Split evaluation (tick_subsets): loop hafnians above 64 subsets (N > 12) run as
+    fixed subset ranges over several ticks. Samples equal those of unsplit serving and of the
+    plain path, in a mix and alone; some chains did wait for their ranges (more ticks than
+    modes)."""
+    from paper_2010_15595_gb300 import sampler as S
+    U, rv, al = _phys(6, 2, r=1.2)
+    st = S.pure_state(U, rv, al)
+    seeds = list(range(40, 52))
+    with S.Sampler(st, cutoff=4, n_cap=30, max_active=128, tick_subsets=64) as smp:
+        rids = [smp.submit(s, 3) for s in seeds]
+        res = [smp.wait(r, timeout=300) for r in rids]
+    split_mix = [r[0] for r in res]
+    assert any(r[1]["ticks"] > 6 for r in res)
+    with S.Sampler(st, cutoff=4, n_cap=30, max_active=128, tick_subsets=64) as smp:
+        split_alone = [_run(smp, [s], n_samples=3)[0] for s in seeds[:4]]
+    with S.Sampler(st, cutoff=4, n_cap=30, max_active=128) as smp:
+        whole = _run(smp, seeds, n_samples=3)
+    with S.Sampler(st, cutoff=4, n_cap=30, batching=False) as plain:
+        alone = _run(plain, seeds, n_samples=3)
+    assert max(int(x.sum(axis=1).max()) for x in whole) > 12  # some loop hafnians were split
+    for a, b, c in zip(split_mix, whole, alone):
+        assert np.array_equal(a, b) and np.array_equal(a, c)
+    for a, b in zip(split_alone, split_mix):
+        assert np.array_equal(a, b)
+
+
 def test_tvd_against_exact_distribution():
     """Fig. 1 setting in small: 3 modes, r = 0.5, cutoff 6; empirical distribution of 20000
     GPU samples vs exact probabilities, against the TVD of exact sampling of the same size."""
