@@ -376,8 +376,9 @@ typedef struct {
    * tick in the tick's batched launch. T > 0 (rounded down to a power of two, at least
    * 64) evaluates a loop hafnian with more than T pair subsets in fixed ranges of T
    * enumeration indices, spread over ticks: each tick runs at most max(T, the subsets of
-   * its batched launch) subsets of such ranges, oldest chains first, and a chain draws its
-   * next photon number once all its candidates are done. This bounds the time of a tick,
+   * its batched launch) subsets of such ranges, oldest chains first (all of them when every
+   * active chain is waiting for ranges), and a chain draws its next photon number once all
+   * its candidates are done. This bounds the time of a tick,
    * so chains with small loop hafnians are not held up by ones with large ones. The
    * ranges depend only on the size and T, so samples stay the same alone and in any mix. */
   size_t tick_subsets;

@@ -49,9 +49,13 @@ __host__ __device__ inline int prec_elem_bytes(int precision) {
   return precision == kPrecC32 ? 8 : (precision == kPrecDD ? 32 : (precision == kPrecTF ? 24 : 16));
 }
 
-// Chunk size of a batched problem with n pairs: a function of n alone.
+// Chunk size of a batched problem with n pairs: a function of n alone (so a problem's
+// result does not depend on its batch), one subset up to n = 10 and 2^(n-10) above, i.e. at
+// most 1024 chunks per problem. A small batch (a serving tick with a few candidates) then
+// spreads each problem over many warps instead of running 64 subsets one after another in
+// one warp; a large batch has chunks enough either way.
 __host__ __device__ inline unsigned long long batch_chunk_size(int n) {
-  return n >= 6 ? 64ull : (1ull << n);
+  return n > 10 ? (1ull << (n - 10)) : 1ull;
 }
 
 // La Budde accumulators P_0..P_t are stored packed: P_u has degree <= u and is kept up to

@@ -436,14 +436,19 @@ int gbsh_sampler::tick(std::vector<Chain>& active) {
   }
 
   // Split candidates: ranges of R enumeration indices, oldest chains first, at most
-  // max(R, batched subsets) subsets in this tick (at least one range).
+  // max(R, batched subsets) subsets in this tick (at least one range) -- unless every active
+  // chain is waiting for ranges, in which case nothing would advance sooner for the limit
+  // and all ranges run.
   if (!splits.empty()) {
     gbsh::DeviceInfo dev;
     e = gbsh::device_info(&dev);
     if (e != cudaSuccess) return from_cuda(e);
     e = gbsh::ensure_constants();
     if (e != cudaSuccess) return from_cuda(e);
-    const uint64_t budget = std::max<uint64_t>(R, batch_subsets);
+    std::vector<char> waits(nch, 0);
+    for (const auto& sp : splits) waits[sp.first] = 1;
+    const bool all_wait = std::all_of(waits.begin(), waits.end(), [](char w) { return w != 0; });
+    const uint64_t budget = all_wait ? ~(uint64_t)0 : std::max<uint64_t>(R, batch_subsets);
     // choose the ranges first, so the workspace and the partial array are sized before the
     // first launch (neither may be reallocated under queued work)
     struct Ran { int chain, j; size_t q; uint64_t i0, i1; };

@@ -80,16 +80,17 @@ def test_split_evaluation_same_samples():
     plain path, in a mix and alone; some chains did wait for their ranges (more ticks than
     modes)."""
     from paper_2010_15595_gb300 import sampler as S
-    U, rv, al = _phys(6, 2, r=1.2)
+    U, rv, al = _phys(8, 2, r=1.2)
     st = S.pure_state(U, rv, al)
     seeds = list(range(40, 52))
     with S.Sampler(st, cutoff=4, n_cap=30, max_active=128, tick_subsets=64) as smp:
-        rids = [smp.submit(s, 3) for s in seeds]
-        res = [smp.wait(r, timeout=300) for r in rids]
-    split_mix = [r[0] for r in res]
-    assert any(r[1]["ticks"] > 6 for r in res)
+        split_mix = _run(smp, seeds, n_samples=3)
     with S.Sampler(st, cutoff=4, n_cap=30, max_active=128, tick_subsets=64) as smp:
-        split_alone = [_run(smp, [s], n_samples=3)[0] for s in seeds[:4]]
+        res = []
+        for s in seeds[:6]:  # one request at a time: the tick's budget is the range size
+            res.append(smp.wait(smp.submit(s, 3), timeout=300))
+    split_alone = [r[0] for r in res]
+    assert any(r[1]["ticks"] > 8 for r in res)
     with S.Sampler(st, cutoff=4, n_cap=30, max_active=128) as smp:
         whole = _run(smp, seeds, n_samples=3)
     with S.Sampler(st, cutoff=4, n_cap=30, batching=False) as plain:
