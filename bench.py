@@ -825,7 +825,7 @@ def main(argv=None):
     p.add_argument("--serve-poisson", type=int, default=60,
                    help="requests per arrival rate (the committed serving profile uses 200)")
     p.add_argument("--serve-rates", type=float, nargs="+", default=[0.5, 1.0, 2.0, 3.0])
-    p.add_argument("--serve-tick-subsets", type=int, default=1 << 14,
+    p.add_argument("--serve-tick-subsets", type=int, default=1 << 16,
                    help="split loop hafnians above this many subsets over ticks (0: off)")
     p.add_argument("--serve-compare", action="store_true",
                    help="also serve without splitting and run the plain path under Poisson arrivals")
