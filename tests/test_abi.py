@@ -84,3 +84,20 @@ def test_autotune_table_emission():
     src = autotune.emit_table(rows, [(fp, 1, 30, 12, 6)], "note")
     assert src.index("{0, 32, 39, 10, 2, 18},") < src.index("{-1, 0, 0, 0, 0, 0},")
     assert "{0, 1, 30, 12, 6}," in src and "// note" in src
+
+
+def test_builtin_tuning_table_applied_by_default():
+    """Every row of the committed measured table (csrc/tuned_gb300.inc) is what the library
+    reports for its sizes in a fresh process state, without any cache file."""
+    import re
+    path = os.path.join(ROOT, "paper_2010_15595_gb300", "csrc", "tuned_gb300.inc")
+    src = open(path).read()
+    single = src.split("kTunedSingle[]")[1].split("};")[0]
+    rows = [tuple(int(x) for x in m.groups())
+            for m in re.finditer(r"\{(-?\d+), (\d+), (\d+), (\d+), (\d+), (\d+)\}", single)]
+    rows = [r for r in rows if r[0] >= 0]
+    assert lib.builtin_tuning_entries() >= len(rows) >= 1
+    for prec, lo, hi, w, ladder, chunks in rows:
+        for N in {lo, (lo + hi) // 2, hi}:
+            lib.set_lhaf_tuning(prec, N)  # reset to the built-in entry
+            assert lib.get_lhaf_tuning(prec, N) == (w, ladder, chunks), (prec, N)
