@@ -30,8 +30,9 @@ struct GraphKey {
   const char *in, *prob, *counter, *partials, *out;
   bool operator==(const GraphKey& o) const {
     return dev == o.dev && count == o.count && n_max == o.n_max && precision == o.precision &&
-           warps == o.warps && warps_small == o.warps_small && total_chunks == o.total_chunks && in == o.in && prob == o.prob &&
-           counter == o.counter && partials == o.partials && out == o.out;
+           warps == o.warps && warps_small == o.warps_small && total_chunks == o.total_chunks &&
+           in == o.in && prob == o.prob && counter == o.counter && partials == o.partials &&
+           out == o.out;
   }
 };
 struct GraphEntry {
