@@ -85,7 +85,7 @@ def lhaf_tf_instr(N: int) -> int:
     return sum(comb(n, k) * subset_tf_instr(k, n) for k in range(1, n + 1))
 
 
-def survey_flops(N: int) -> float:
+def householder_flops(N: int) -> float:
     """The fixed per-subset convention F(m, n) = (40/3) m^3 + (4/3) m^3 + 8 n m^2 + 4 n^2
     (m = 2k: a Householder Hessenberg reduction, La Budde, explicit loop matvecs, the
     exp-polynomial), summed over the subsets. It counts a different algorithm from the
