@@ -556,11 +556,7 @@ __device__ __noinline__ Term subset_term_full(const Problem& P, uint64_t z, int 
       // scaled pivot row u_j = H[c+1][j] / b, j >= c+1. u_{c+1} is only an operand of the
       // elimination (the diagonal entry itself is unchanged by the similarity) and is
       // parked in the subdiagonal slot H[c+1][c], which is never read again.
-      T rinv;
-      if constexpr (std::is_same<T, tfc>::value)
-        rinv = n <= 20 ? crecip_small(bp) : crecip(bp);  // see crecip_small
-      else
-        rinv = crecip(bp);
+      const T rinv = crecip(bp);
       for_rolled<T>(c + 1 + lane, S, 32, [&](int j) {
         const T u = cmul(H[(c + 1) * ldh + j], rinv);
         H[(c + 1) * ldh + (j == c + 1 ? c : j)] = u;

@@ -146,14 +146,19 @@ __device__ __forceinline__ tf3 tf_scale2(tf3 x, int s) {
              __fmul_rn(__fmul_rn(x.c, f1), f2));
 }
 
+// out-of-line copies for the once-per-step code (pivot reciprocal): small footprint
+__device__ __noinline__ tf3 tf_fma_ool(tf3 x, tf3 y, tf3 acc) { return tf_fma(x, y, acc); }
+__device__ __noinline__ tf3 tf_mul_ool(tf3 x, tf3 y) { return x * y; }
 // 1/x by Newton's iteration r <- r + r (1 - x r) from the FP32 reciprocal of the leading
 // word; each step doubles the correct bits (24 -> 48 -> 96, limited by the format).
 __device__ __forceinline__ tf3 tf_recip(tf3 x) {
   tf3 r(__frcp_rn(x.a));
   const tf3 one(1.0f);
+  const tf3 mx = -x;
+#pragma unroll 1
   for (int it = 0; it < 2; ++it) {
-    const tf3 e = tf_fma(-x, r, one);
-    r = tf_fma(r, e, r);
+    const tf3 e = tf_fma_ool(mx, r, one);
+    r = tf_fma_ool(r, e, r);
   }
   return r;
 }
@@ -200,30 +205,16 @@ __device__ __forceinline__ tfc cmul(tfc p, tfc q) {
   return cfma(tfc{z, z}, p, q);
 }
 __device__ __noinline__ tfc cscale(tfc p, tf3 s) { return tfc{p.x * s, p.y * s}; }
-// out of line as well: ~450 instructions once per elimination step (2 % faster at N = 40)
+// The pivot reciprocal 1/p = conj(p) / |p|^2, out of line, with a small footprint: |p|^2
+// through the shared multiply-add, the Newton steps and the final products through single
+// out-of-line copies (the same operations on the same operands as an inline form, so
+// bit-identical to it). It runs once per elimination step, and its code displaces the hot
+// loops' in the instruction cache: 3 KB instead of 7.4 KB inline made GB300's N = 32 5 % and
+// N = 40 2.4 % faster (N = 50 1.2 % slower).
 __device__ __noinline__ tfc crecip(tfc p) {
-  const tf3 d = tf_dot2(p.x, p.x, p.y, p.y, tf3(0.0f));
-  const tf3 r = tf_recip(d);
-  return tfc{p.x * r, -(p.y * r)};
-}
-// The same reciprocal with a third of the code: |p|^2 through the shared multiply-add, the
-// Newton steps and the final products through single out-of-line copies (bit-identical:
-// the same operations on the same operands). It runs once per elimination step and its
-// code displaces the hot loops' in the instruction cache, so the small footprint wins while
-// the per-subset work is small (GB300: N = 32 -5 %, N = 40 -2.4 %), and the inline form
-// wins above (N = 50 +1.2 % with the small one).
-__device__ __noinline__ tf3 tf_fma_ool(tf3 x, tf3 y, tf3 acc) { return tf_fma(x, y, acc); }
-__device__ __noinline__ tf3 tf_mul_ool(tf3 x, tf3 y) { return x * y; }
-__device__ __noinline__ tfc crecip_small(tfc p) {
   const tf3 z(0.0f);
   const tf3 d = -cfms(tfc{z, z}, p, tfc{p.x, -p.y}).x;  // p conj(p) = |p|^2
-  tf3 r(__frcp_rn(d.a));
-  const tf3 one(1.0f), md = -d;
-#pragma unroll 1
-  for (int it = 0; it < 2; ++it) {  // r <- r + r (1 - d r), as tf_recip
-    const tf3 e = tf_fma_ool(md, r, one);
-    r = tf_fma_ool(r, e, r);
-  }
+  const tf3 r = tf_recip(d);
   return tfc{tf_mul_ool(p.x, r), -tf_mul_ool(p.y, r)};
 }
 // exact power-of-two scaling of both parts, out of line like the operations above
